@@ -1,0 +1,397 @@
+"""Benchmark of the fused d2v9 stream-collide step (lattice updates per second).
+
+Default workload: the 4096 x 4096 periodic lattice with a density step at
+x = L/2 (n = 1.0 | 0.8) and a smooth temperature field t in [0.01, 0.2] from 8
+seeded Fourier modes, tau = 0.8, Fermi-Dirac statistics with the per-cell
+inversion, populations stored as FP32 deviations.  One bench step is one LBGK
+update of every cell.  The population buffers (1.2 GB) exceed L2, so no flush
+is needed between steps.
+
+Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline; surrogate+FP32 vs plain FP64 GPU at stated error"
+BYTES_PER_ELEM = {"f64": 8, "f32": 4, "bf16": 2}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="f32", choices=["f32", "bf16", "f64"])
+    ap.add_argument("--L", type=int, default=4096)
+    ap.add_argument("--tau", type=float, default=0.8)
+    ap.add_argument("--no-extras", action="store_true", help="skip FP64 comparison, e2e and CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload_config(a, world):
+    return {
+        "workload": f"smooth_t_{a.L}x{a.L}",
+        "lattice": [a.L, a.L],
+        "cells": a.L * a.L,
+        "stencil": "d2v9 K=3 generalized-polynomial LBGK, FD statistics, per-cell J2->x inversion",
+        "storage": {"f32": "FP32 deviations g = f - W_ref", "bf16": "BF16 deviations", "f64": "FP64 f"}[a.prec],
+        "tau": a.tau,
+        "t_range": [0.01, 0.2],
+        "density_step": [1.0, 0.8],
+        "boundaries": "periodic",
+        "l2": f"inputs larger than L2 ({2 * 9 * a.L * a.L * BYTES_PER_ELEM[a.prec] / 1e9:.2f} GB population buffers)",
+        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+    }
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if "Active" in s[3 + k]
+                          and "Not" not in s[3 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_setup(a):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if a.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("lbm_dev32.cuh", "lbm_kernels.cuh", "fd_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1510_07328_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, cells: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the kernel source as it is now (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+        e = d[kernel]
+        if e["source_hash"] != kernel_source_hash():
+            return None
+        return e["dram_bytes_per_cell"] * cells
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- oracle arm
+
+
+def oracle_sample_mlups(L: int, tau: float, seconds: float, window: int = 48):
+    """Time the CPU oracle on a window of the workload (periodic window
+    stand-in), as many steps as fit in ~`seconds`."""
+    from oracle import lbm as olbm
+    from paper_1510_07328_gb300 import inputs
+
+    t = inputs.smooth_t_field(L, rows=slice(L // 2 - window // 2, L // 2 + window // 2))
+    x0 = L // 2 - window // 2
+    t = t[:, x0:x0 + window]
+    xs = np.arange(x0, x0 + window)
+    n = np.where(xs < L // 2, 1.0, 0.8)[None, :].repeat(window, 0)
+    z = np.zeros_like(n)
+    f = olbm.init_equilibrium(n, z, z, t)
+    p = olbm.Params(tau=tau)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        f = olbm.step(f, p)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return window * window * steps / el / 1e6, steps, window, el
+
+
+def run_reference(a, world, rank):
+    if rank != 0:
+        return
+    from oracle import lbm as olbm
+    from paper_1510_07328_gb300 import inputs
+
+    window = 32
+    t = inputs.smooth_t_field(a.L, rows=slice(a.L // 2 - window // 2, a.L // 2 + window // 2))
+    x0 = a.L // 2 - window // 2
+    t = t[:, x0:x0 + window]
+    xs = np.arange(x0, x0 + window)
+    n = np.where(xs < a.L // 2, 1.0, 0.8)[None, :].repeat(window, 0)
+    z = np.zeros_like(n)
+    f = olbm.init_equilibrium(n, z, z, t)
+    p = olbm.Params(tau=a.tau)
+    for _ in range(a.warmup):
+        f = olbm.step(f, p)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        f = olbm.step(f, p)
+    el = time.perf_counter() - t0
+    mlups = window * window * a.steps / el / 1e6
+    cfg = workload_config(a, 1)
+    sample = f"{window}x{window} window of the lattice at x = L/2 (periodic wrap), {a.steps} steps"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": 0,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": el / a.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "config": cfg,
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------- GPU arm
+
+
+def run_ours(a, world, rank, local):
+    import torch
+
+    from paper_1510_07328_gb300 import build, inputs
+
+    build.build()
+    from paper_1510_07328_gb300 import lbm
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    prob = inputs.smooth_t(a.L, tau=a.tau)
+    cells = prob.cells
+    cfg = workload_config(a, world)
+    # inputs resident in HBM before the timed region
+    dev_fields = {k: torch.from_numpy(getattr(prob, k)).cuda() for k in ("n", "ux", "uy", "t")}
+    torch.cuda.synchronize()
+    lat = lbm.Lattice([prob], stat="fd", prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05)
+    with torch.cuda.stream(stream):
+        lat.init(fields_on_device=dev_fields)
+        lat.step(a.warmup)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.15)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    l0 = lbm.lbm_launch_count(lat.ctx)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    lat.step(a.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    sampler.stop()
+    launches = lbm.lbm_launch_count(lat.ctx) - l0
+    ms_max = max_over_ranks(world, ms)
+    fl = lat.fields(0, diag=True)
+    nonfinite = fl["diag"]["nonfinite"] / cells
+    clamped = fl["diag"]["clamped"] / cells
+    lat.close()
+
+    value = world * cells * a.steps / (ms_max / 1e3) / 1e6
+    per_launch_s = ms / 1e3 / a.steps
+    bytes_per_cell = 18 * BYTES_PER_ELEM[a.prec]
+    achieved = bytes_per_cell * cells / per_launch_s / 1e9
+    peak, peak_kind = peaks()
+    kname = {"f32": "stream_collide_dev<float,FD>", "bf16": "stream_collide_dev<bf16,FD>",
+             "f64": "stream_collide_f64<FD>"}[a.prec]
+    traffic = profiled_traffic(kname, cells)
+    out = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"f32": "f32", "bf16": "f32 (bf16 storage)", "f64": "f64"}[a.prec],
+        "data": "synthetic (seeded SplitMix64 fields)", "config": cfg,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "traffic": traffic,
+                     "algorithmic_bytes_per_cell": bytes_per_cell, "kernel": kname},
+        "gpu_launches": launches,
+        "clocks": sampler.summary(),
+        "state_after_timed_steps": {"nonfinite_frac": nonfinite, "clamped_frac": clamped},
+    }
+    if not a.no_extras and rank == 0:
+        out.update(extras(a, prob, dev_fields, lbm, torch, stream, value))
+    del dev_fields
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def extras(a, prob, dev_fields, lbm, torch, stream, value):
+    """FP64 comparison on the same lattice, end-to-end timing through host
+    buffers, and the CPU oracle on a bounded sample."""
+    res = {}
+    cells = prob.cells
+    # plain FP64 GPU path, same lattice
+    k64 = 20
+    lat64 = lbm.Lattice([prob], stat="fd", prec="f64", stream=stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        lat64.init(fields_on_device=dev_fields)
+        lat64.step(2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat64.step(k64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    v64 = cells * k64 / (e0.elapsed_time(e1) / 1e3) / 1e6
+    res["fp64_gpu"] = {"value": v64, "unit": "MLUPS", "steps": k64}
+    res["speedup_vs_fp64"] = value / v64
+    # field error of the reduced-precision path against FP64 after N steps
+    nerr = 20
+    lr = lbm.Lattice([prob], stat="fd", prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05)
+    with torch.cuda.stream(stream):
+        lr.init(fields_on_device=dev_fields)
+        lat64.init(fields_on_device=dev_fields)
+        lr.step(nerr)
+        lat64.step(nerr)
+    torch.cuda.synchronize()
+    fa = {k: torch.empty((prob.ny, prob.nx), dtype=torch.float64, device="cuda") for k in ("n", "ux", "uy", "T")}
+    fb = {k: torch.empty_like(v) for k, v in fa.items()}
+    with torch.cuda.stream(stream):
+        lbm.lbm_moments(lr.ctx, 0, n=fa["n"], ux=fa["ux"], uy=fa["uy"], T=fa["T"], on_device=True)
+        lbm.lbm_moments(lat64.ctx, 0, n=fb["n"], ux=fb["ux"], uy=fb["uy"], T=fb["T"], on_device=True)
+    torch.cuda.synchronize()
+    ok = torch.isfinite(fb["n"]) & torch.isfinite(fa["n"]) & torch.isfinite(fb["T"]) & torch.isfinite(fa["T"])
+    err = {"steps": nerr, "finite_frac": float(ok.double().mean())}
+    for k in ("n", "T"):
+        d = (fa[k] - fb[k])[ok].abs()
+        err[f"{k}_max_abs"] = float(d.max())
+        err[f"{k}_max_rel"] = float((d / fb[k][ok].abs()).max())
+    du = torch.sqrt((fa["ux"] - fb["ux"]) ** 2 + (fa["uy"] - fb["uy"]) ** 2)[ok]
+    err["u_max_abs"] = float(du.max())
+    res["field_error_vs_fp64"] = err
+    lr.close()
+    lat64.close()
+    del fa, fb
+    # end to end through the public API with host buffers: H2D of the initial
+    # fields, K steps, D2H of the moments
+    host = {k: np.ascontiguousarray(getattr(prob, k)) for k in ("n", "ux", "uy", "t")}
+    outs = {k: np.empty((prob.ny, prob.nx)) for k in ("n", "ux", "uy", "T")}
+    le = lbm.Lattice([prob], stat="fd", prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    le.init()  # host fields -> device inside the call
+    le.step(a.steps)
+    lbm.lbm_moments(le.ctx, 0, **outs)  # device -> host, synchronises
+    el = time.perf_counter() - t0
+    le.close()
+    h2d = 4 * cells * 8
+    d2h = 4 * cells * 8
+    res["e2e"] = {"value": cells * a.steps / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / a.steps,
+                  "d2h_bytes_per_step": d2h / a.steps,
+                  "note": "init from host fields + steps + moments to host, wall clock"}
+    # CPU oracle on a bounded sample
+    mlups, steps, window, el = oracle_sample_mlups(a.L, a.tau, a.cpu_seconds)
+    res["cpu_baseline"] = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                           "sample": f"{window}x{window} window at x = L/2, {steps} steps in {el:.1f} s"}
+    return res
+
+
+def main():
+    a = parse()
+    world, rank, local = dist_setup(a)
+    if a.impl == "reference":
+        run_reference(a, world, rank)
+    else:
+        run_ours(a, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * lbm.h - C ABI of the GB300 lattice Boltzmann library for the method of
+ * Coelho, Ilha and Doria, "A lattice Boltzmann method based on generalized
+ * polynomials and its application for electrons in metals" (arXiv:1510.07328).
+ *
+ * The library advances d2v9 populations with the K = 3 equilibrium expanded in
+ * polynomials orthonormal under the Fermi-Dirac equilibrium itself
+ * (Eq. (expansao0); the geometric-velocity form printed in Sect. "The Gaussian
+ * quadrature"), relaxed by BGK (the LBGK equation of the same section) after
+ * pull streaming.  Per cell and step it gathers the nine populations, forms
+ * n = I_0, u_0 = j/n (the moment update after the LBGK equation) and the
+ * energy E = sum f |e|^2, reads J_2 = 3 (E/n - |u_0|^2)/D, inverts the
+ * Fermi-Dirac moment ratio J_2(x) = f_2^2/(f_1 f_3) for x = mu/theta
+ * (I_2N = (2 pi)^{D/2} theta^{N+D/2} f_{N+D/2}(x), Sect. "Generalized
+ * polynomials in D dimensions"), evaluates J_4 = f_3^2/(f_2 f_4), builds f_eq
+ * and relaxes.
+ *
+ * Conventions shared by every call:
+ *  - Velocity order a = 0..8: rest; (1,0), (0,1), (-1,0), (0,-1);
+ *    (1,1), (-1,1), (-1,-1), (1,-1).
+ *  - Arrays of per-cell values are row-major [ny][nx] (x fastest), one array
+ *    per problem; populations are [9][ny][nx].
+ *  - All calls are asynchronous on the context's CUDA stream unless stated;
+ *    a call that writes host memory synchronises that stream before it returns.
+ *  - Every call returns an lbm_status; nothing aborts or throws.  On failure
+ *    lbm_last_error() returns a message (per context; lbm_last_error(NULL)
+ *    gives the last failure of lbm_create).  An asynchronous CUDA error
+ *    surfaces at the next call that synchronises (LBM_ECUDA).
+ *  - Pointers are plain host or device addresses as stated per argument; the
+ *    library never frees memory it did not allocate.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque; owned by the library */
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,       /* bad argument: NULL, size, tau <= 1/2, n <= 0, t out of range */
+  LBM_ENOMEM = 2,       /* device or host allocation failed */
+  LBM_ECUDA = 3,        /* a CUDA call failed (message in lbm_last_error) */
+  LBM_ETIMEOUT = 4,     /* a bounded device wait gave up */
+  LBM_EUNSUPPORTED = 5  /* valid but not implemented combination */
+} lbm_status;
+
+/* Statistics of the weight / equilibrium (Sect. "Generalized polynomials in D
+ * dimensions").  FD: J_2 from the energy moment, J_4 from the inverted x.
+ * FD_T0: the theta = 0 closure of Sect. "Numerical simulations for electrons
+ * in metals", J_N = 1 + 2/(N + D) constant.  MB: J_N = 1, the Hermite D2Q9
+ * limit. */
+typedef enum { LBM_STAT_FD = 0, LBM_STAT_FD_T0 = 1, LBM_STAT_MB = 2 } lbm_stat;
+
+/* Population storage.  F64: f itself in FP64, all arithmetic FP64.
+ * F32_DEV / BF16_DEV: the deviation g_a = f_a - W_a^ref from a per-problem
+ * constant W^ref = w_a(J_2(t_ref)) n_ref, stored in FP32 / BF16, moment sums
+ * and equilibrium in FP32. */
+typedef enum { LBM_F64 = 0, LBM_F32_DEV = 1, LBM_BF16_DEV = 2 } lbm_prec;
+
+typedef enum { LBM_INV_EXACT = 0, LBM_INV_SURROGATE = 1 } lbm_inv;
+
+typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_BOUNCEBACK = 1 } lbm_bc;
+
+/* One lattice.  bc_*: LBM_BC_*; halfway bounce-back walls sit half a cell
+ * outside the first and last row/column.  n_ref, t_ref: the reference state
+ * of the deviation storage (ignored for LBM_F64; n_ref > 0, t_ref in
+ * [1e-3, 10]). */
+typedef struct {
+  int32_t nx, ny;
+  double tau;
+  int32_t bc_x, bc_y;
+  double n_ref, t_ref;
+} lbm_problem;
+
+typedef struct {
+  int32_t dim;       /* 2 (d2v9); other values -> LBM_EUNSUPPORTED */
+  int32_t order;     /* 3 (K = 3 expansion); other values -> LBM_EUNSUPPORTED */
+  int32_t stat;      /* lbm_stat */
+  int32_t prec;      /* lbm_prec */
+  int32_t inv;       /* lbm_inv */
+  int32_t nproblems; /* >= 1; all problems advance together in one launch per step */
+  const lbm_problem* problems; /* host array of nproblems entries, copied */
+} lbm_params;
+
+/* lbm_create: validate p, allocate the two population buffers and tables on
+ * the current CUDA device, and bind the context to `cuda_stream` (a
+ * cudaStream_t; NULL = legacy default stream).  Populations start at zero;
+ * call lbm_init_riemann for every problem before stepping.
+ * Errors: LBM_EINVAL (p or out NULL, nx or ny < 1, tau <= 0.5, bad enum,
+ * reference state out of range), LBM_EUNSUPPORTED (dim != 2, order != 3),
+ * LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out);
+
+/* Initial state of one problem (the Riemann problems of Sect. "Numerical
+ * simulations for electrons in metals" and their 2D analogues).  The
+ * populations are set to the equilibrium f_eq(n, u_0, t) of each cell.
+ *  HALF:     s[0] for x < x0, s[1] for x >= x0.
+ *  QUADRANT: s[q], q = (x >= x0) + 2 (y >= y0).
+ *  FIELD:    per-cell arrays n, ux, uy, t of nx*ny doubles each, host or
+ *            device memory per field_on_device; read during the call only.
+ * t is T/T_F (T_F the theta = 0 chemical potential at the cell's density);
+ * it must lie in [1e-3, 10] for LBM_STAT_FD and is ignored otherwise. */
+typedef enum { LBM_INIT_HALF = 0, LBM_INIT_QUADRANT = 1, LBM_INIT_FIELD = 2 } lbm_init_kind;
+typedef struct { double n, ux, uy, t; } lbm_state;
+typedef struct {
+  int32_t kind;
+  int32_t x0, y0;
+  lbm_state s[4];
+  const double* n;
+  const double* ux;
+  const double* uy;
+  const double* t;
+  int32_t field_on_device;
+} lbm_riemann_desc;
+
+/* Errors: LBM_EINVAL (problem index, kind, NULL field, n <= 0 or t out of
+ * range in a region state; per-cell field values are not checked on the
+ * host), LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_init_riemann(lbm_ctx* ctx, int32_t problem, const lbm_riemann_desc* d);
+
+/* Advance every problem by nsteps LBGK steps (pull stream + collide, one
+ * kernel launch per step; repeated steps replay a captured CUDA graph).
+ * Asynchronous.  Errors: LBM_EINVAL (nsteps < 0), LBM_ECUDA. */
+lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps);
+
+/* Per-run diagnostics of lbm_moments: totals over the problem's cells (FP64,
+ * summed in a fixed order, so identical states give identical sums) and
+ * counts of cells whose inversion was clamped to t in [1e-3, 10] or whose
+ * state is not finite. */
+typedef struct {
+  double sum_n, sum_jx, sum_jy, sum_E;
+  int64_t clamped;
+  int64_t nonfinite;
+} lbm_diag;
+
+/* Macroscopic fields of one problem from the current populations, each an
+ * array of nx*ny doubles (any pointer may be NULL to skip that field):
+ *  n; u_0 = (ux, uy) in lattice units; T = theta and mu in the paper's
+ *  dimensionless units (m = k_B = hbar = 1); t = T/T_F.  For LBM_STAT_FD_T0,
+ *  T = t = 0 and mu = T_F = n/(2 pi); for LBM_STAT_MB, T, mu, t are NaN.
+ * out_on_device != 0: the pointers are device memory and the call is
+ * asynchronous; otherwise host memory and the call synchronises.  diag may be
+ * NULL; if not, the call synchronises and fills it (host memory). */
+lbm_status lbm_moments(lbm_ctx* ctx, int32_t problem, double* n, double* ux, double* uy,
+                       double* T, double* mu, double* t, int32_t out_on_device, lbm_diag* diag);
+
+/* Checkpoint / resume: copy the populations f_a (FP64, [9][ny][nx]) of one
+ * problem out of or into the library.  Storage of reduced precision converts
+ * (f = W^ref + g on the way out, g = f - W^ref rounded on the way in).
+ * on_device selects device or host memory for f; host copies synchronise. */
+lbm_status lbm_get_populations(lbm_ctx* ctx, int32_t problem, double* f, int32_t on_device);
+lbm_status lbm_set_populations(lbm_ctx* ctx, int32_t problem, const double* f, int32_t on_device);
+
+/* Release everything the context owns (synchronises its stream first). */
+lbm_status lbm_destroy(lbm_ctx* ctx);
+
+/* Message of the last failure on ctx (or of lbm_create if ctx is NULL);
+ * valid until the next call on the same context. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Number of kernel launches issued by the library on this context since it
+ * was created (graph replays count each captured kernel). */
+int64_t lbm_launch_count(const lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

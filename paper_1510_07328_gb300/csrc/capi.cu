@@ -1,0 +1,463 @@
+// C ABI of the library (declared in include/lbm.h): contexts, buffers,
+// dispatch of the kernels in lbm_kernels.cuh, CUDA-graph replay of steps.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_kernels.cuh"
+#include "lbm_dev32.cuh"
+
+using namespace lbm;
+
+namespace {
+
+constexpr int kGraphChunk = 16;  // steps per captured graph (even: buffers return)
+
+std::mutex g_err_mu;
+std::string g_create_err;
+
+size_t elem_size(int prec) { return prec == LBM_F64 ? 8 : prec == LBM_F32_DEV ? 4 : 2; }
+
+}  // namespace
+
+struct lbm_ctx {
+  int stat = 0, prec = 0, inv = 0, nprob = 0;
+  std::vector<lbm_problem> probs;
+  std::vector<ProbDev> ph;  // host copy of the device table
+  ProbDev* pd = nullptr;
+  int64_t plane = 0, ntiles = 0;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  InvLimits lim{};
+  InvLimits* lim_d = nullptr;
+  double* partials = nullptr;
+  int64_t partials_cap = 0;
+  double* diag_d = nullptr;
+  double* tmp = nullptr;
+  int64_t tmp_cap = 0;
+  int64_t launches = 0;
+  std::string err;
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx* ctx, lbm_status s, const std::string& m) {
+  if (ctx) {
+    ctx->err = m;
+  } else {
+    std::lock_guard<std::mutex> g(g_err_mu);
+    g_create_err = m;
+  }
+  return s;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) return fail(ctx, LBM_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define CKL()                                                                           \
+  do {                                                                                  \
+    cudaError_t e_ = cudaGetLastError();                                                \
+    if (e_ != cudaSuccess) return fail(ctx, LBM_ECUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <int STAT>
+void launch_step_stat(lbm_ctx* c, const void* in, void* out, cudaStream_t s) {
+  const unsigned g = (unsigned)c->ntiles;
+  switch (c->prec) {
+    case LBM_F64:
+      stream_collide_f64<STAT><<<g, kTileX, 0, s>>>((const double*)in, (double*)out, c->pd, c->nprob, c->plane, c->lim);
+      break;
+    case LBM_F32_DEV:
+      stream_collide_dev<float, STAT><<<g, kTileX, 0, s>>>((const float*)in, (float*)out, c->pd, c->nprob, c->plane,
+                                                             c->lim);
+      break;
+    default:
+      stream_collide_dev<__nv_bfloat16, STAT><<<g, kTileX, 0, s>>>((const __nv_bfloat16*)in, (__nv_bfloat16*)out,
+                                                                     c->pd, c->nprob, c->plane, c->lim);
+      break;
+  }
+}
+
+void launch_step(lbm_ctx* c, const void* in, void* out, cudaStream_t s) {
+  switch (c->stat) {
+    case LBM_STAT_FD: launch_step_stat<STAT_FD>(c, in, out, s); break;
+    case LBM_STAT_FD_T0: launch_step_stat<STAT_T0>(c, in, out, s); break;
+    default: launch_step_stat<STAT_MB>(c, in, out, s); break;
+  }
+}
+
+template <class T>
+void launch_init_t(lbm_ctx* c, const ProbDev& P, const InitDesc& d) {
+  const int64_t cells = (int64_t)P.nx * P.ny;
+  T* f = (T*)c->buf[c->cur];
+  const unsigned g = blocks_for(cells, 256);
+  switch (c->stat) {
+    case LBM_STAT_FD: init_kernel<T, STAT_FD><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
+    case LBM_STAT_FD_T0: init_kernel<T, STAT_T0><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
+    default: init_kernel<T, STAT_MB><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
+  }
+}
+
+template <class T, int STAT>
+void launch_moments_t(lbm_ctx* c, const ProbDev& P, double* o[6], unsigned g) {
+  moments_kernel<T, STAT><<<g, kMomThreads, 0, c->stream>>>((const T*)c->buf[c->cur], P, c->plane, c->lim, o[0], o[1],
+                                                             o[2], o[3], o[4], o[5], c->partials);
+}
+
+template <class T>
+void launch_moments_p(lbm_ctx* c, const ProbDev& P, double* o[6], unsigned g) {
+  switch (c->stat) {
+    case LBM_STAT_FD: launch_moments_t<T, STAT_FD>(c, P, o, g); break;
+    case LBM_STAT_FD_T0: launch_moments_t<T, STAT_T0>(c, P, o, g); break;
+    default: launch_moments_t<T, STAT_MB>(c, P, o, g); break;
+  }
+}
+
+lbm_status ensure_tmp(lbm_ctx* ctx, int64_t doubles) {
+  if (ctx->tmp_cap >= doubles) return LBM_OK;
+  if (ctx->tmp) CK(cudaFree(ctx->tmp));
+  ctx->tmp = nullptr;
+  ctx->tmp_cap = 0;
+  CK(cudaMalloc(&ctx->tmp, (size_t)doubles * sizeof(double)));
+  ctx->tmp_cap = doubles;
+  return LBM_OK;
+}
+
+bool valid_t(double t) { return t >= kTMin && t <= kTMax; }
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_last_error(const lbm_ctx* ctx) {
+  if (ctx) return ctx->err.c_str();
+  std::lock_guard<std::mutex> g(g_err_mu);
+  return g_create_err.c_str();
+}
+
+int64_t lbm_launch_count(const lbm_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
+  lbm_ctx* ctx = nullptr;
+  if (!p || !out) return fail(nullptr, LBM_EINVAL, "lbm_create: NULL argument");
+  *out = nullptr;
+  if (p->dim != 2) return fail(nullptr, LBM_EUNSUPPORTED, "lbm_create: only dim = 2 (d2v9) is implemented");
+  if (p->order != 3) return fail(nullptr, LBM_EUNSUPPORTED, "lbm_create: only order K = 3 is implemented");
+  if (p->stat < 0 || p->stat > 2) return fail(nullptr, LBM_EINVAL, "lbm_create: bad stat");
+  if (p->prec < 0 || p->prec > 2) return fail(nullptr, LBM_EINVAL, "lbm_create: bad prec");
+  if (p->inv != LBM_INV_EXACT && p->inv != LBM_INV_SURROGATE) return fail(nullptr, LBM_EINVAL, "lbm_create: bad inv");
+  if (p->inv == LBM_INV_SURROGATE)
+    return fail(nullptr, LBM_EUNSUPPORTED, "lbm_create: the surrogate inversion is not built into this library");
+  if (p->nproblems < 1 || !p->problems) return fail(nullptr, LBM_EINVAL, "lbm_create: no problems");
+  for (int i = 0; i < p->nproblems; ++i) {
+    const lbm_problem& q = p->problems[i];
+    if (q.nx < 1 || q.ny < 1) return fail(nullptr, LBM_EINVAL, "lbm_create: nx, ny must be >= 1");
+    if ((int64_t)q.nx * q.ny > ((int64_t)1 << 40)) return fail(nullptr, LBM_EINVAL, "lbm_create: problem too large");
+    if (!(q.tau > 0.5) || !std::isfinite(q.tau)) return fail(nullptr, LBM_EINVAL, "lbm_create: tau must be > 1/2");
+    if ((q.bc_x != 0 && q.bc_x != 1) || (q.bc_y != 0 && q.bc_y != 1))
+      return fail(nullptr, LBM_EINVAL, "lbm_create: bad boundary kind");
+    if (p->prec != LBM_F64) {
+      if (!(q.n_ref > 0.0) || !std::isfinite(q.n_ref)) return fail(nullptr, LBM_EINVAL, "lbm_create: n_ref must be > 0");
+      if (p->stat == LBM_STAT_FD && !valid_t(q.t_ref))
+        return fail(nullptr, LBM_EINVAL, "lbm_create: t_ref must lie in [1e-3, 10]");
+    }
+  }
+  ctx = new (std::nothrow) lbm_ctx();
+  if (!ctx) return fail(nullptr, LBM_ENOMEM, "lbm_create: host allocation failed");
+  ctx->stat = p->stat;
+  ctx->prec = p->prec;
+  ctx->inv = p->inv;
+  ctx->nprob = p->nproblems;
+  ctx->probs.assign(p->problems, p->problems + p->nproblems);
+  ctx->stream = (cudaStream_t)cuda_stream;
+  int64_t base = 0, tiles = 0;
+  for (int i = 0; i < ctx->nprob; ++i) {
+    const lbm_problem& q = ctx->probs[i];
+    ProbDev d{};
+    d.nx = q.nx;
+    d.ny = q.ny;
+    d.pitch = (q.nx + 31) / 32 * 32;
+    d.bc_x = q.bc_x;
+    d.bc_y = q.bc_y;
+    d.tiles_x = (q.nx + kTileX - 1) / kTileX;
+    d.base = base;
+    d.tile_begin = tiles;
+    d.tau = q.tau;
+    d.omega = 1.0 / q.tau;
+    d.n_ref = p->prec == LBM_F64 ? 0.0 : q.n_ref;
+    d.t_ref = p->prec == LBM_F64 ? 0.0 : q.t_ref;
+    base += (int64_t)d.pitch * q.ny;
+    tiles += (int64_t)d.tiles_x * q.ny;
+    ctx->ph.push_back(d);
+  }
+  ctx->plane = (base + 31) / 32 * 32;
+  ctx->ntiles = tiles;
+  if (tiles > 0x7fffffffLL) {
+    delete ctx;
+    return fail(nullptr, LBM_EINVAL, "lbm_create: lattice too large for one launch");
+  }
+  auto cleanup = [&](lbm_status s, const std::string& m) {
+    lbm_destroy(ctx);
+    return fail(nullptr, s, m);
+  };
+  const size_t bytes = (size_t)ctx->plane * 9 * elem_size(ctx->prec);
+  for (int b = 0; b < 2; ++b) {
+    cudaError_t e = cudaMalloc(&ctx->buf[b], bytes);
+    if (e != cudaSuccess) return cleanup(LBM_ENOMEM, std::string("lbm_create: population buffers: ") + cudaGetErrorString(e));
+    e = cudaMemsetAsync(ctx->buf[b], 0, bytes, ctx->stream);
+    if (e != cudaSuccess) return cleanup(LBM_ECUDA, std::string("lbm_create: memset: ") + cudaGetErrorString(e));
+  }
+  cudaError_t e = cudaMalloc(&ctx->pd, sizeof(ProbDev) * ctx->nprob);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->lim_d, sizeof(InvLimits));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->diag_d, sizeof(double) * kNPartial);
+  if (e != cudaSuccess) return cleanup(LBM_ENOMEM, std::string("lbm_create: tables: ") + cudaGetErrorString(e));
+  e = cudaMemcpyAsync(ctx->pd, ctx->ph.data(), sizeof(ProbDev) * ctx->nprob, cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) return cleanup(LBM_ECUDA, std::string("lbm_create: upload: ") + cudaGetErrorString(e));
+  setup_kernel<<<1, 1, 0, ctx->stream>>>(ctx->lim_d);
+  ref_kernel<<<blocks_for(ctx->nprob, 64), 64, 0, ctx->stream>>>(ctx->pd, ctx->nprob, ctx->stat);
+  ctx->launches += 2;
+  e = cudaMemcpyAsync(&ctx->lim, ctx->lim_d, sizeof(InvLimits), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->ph.data(), ctx->pd, sizeof(ProbDev) * ctx->nprob, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cleanup(LBM_ECUDA, std::string("lbm_create: setup: ") + cudaGetErrorString(e));
+  e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cleanup(LBM_ECUDA, std::string("lbm_create: stream: ") + cudaGetErrorString(e));
+  *out = ctx;
+  return LBM_OK;
+}
+
+lbm_status lbm_init_riemann(lbm_ctx* ctx, int32_t problem, const lbm_riemann_desc* d) {
+  if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_init_riemann: NULL context");
+  if (!d) return fail(ctx, LBM_EINVAL, "lbm_init_riemann: NULL descriptor");
+  if (problem < 0 || problem >= ctx->nprob) return fail(ctx, LBM_EINVAL, "lbm_init_riemann: bad problem index");
+  const ProbDev& P = ctx->ph[problem];
+  const int64_t cells = (int64_t)P.nx * P.ny;
+  InitDesc k{};
+  k.kind = d->kind;
+  k.x0 = d->x0;
+  k.y0 = d->y0;
+  if (d->kind == LBM_INIT_HALF || d->kind == LBM_INIT_QUADRANT) {
+    const int ns = d->kind == LBM_INIT_HALF ? 2 : 4;
+    for (int r = 0; r < ns; ++r) {
+      const lbm_state& s = d->s[r];
+      if (!(s.n > 0.0) || !std::isfinite(s.n) || !std::isfinite(s.ux) || !std::isfinite(s.uy))
+        return fail(ctx, LBM_EINVAL, "lbm_init_riemann: region state needs n > 0 and finite u");
+      if (ctx->stat == LBM_STAT_FD && !valid_t(s.t))
+        return fail(ctx, LBM_EINVAL, "lbm_init_riemann: t must lie in [1e-3, 10]");
+      k.s[r][0] = s.n;
+      k.s[r][1] = s.ux;
+      k.s[r][2] = s.uy;
+      k.s[r][3] = s.t;
+    }
+  } else if (d->kind == LBM_INIT_FIELD) {
+    if (!d->n || !d->ux || !d->uy || !d->t) return fail(ctx, LBM_EINVAL, "lbm_init_riemann: NULL field array");
+    if (d->field_on_device) {
+      k.n = d->n;
+      k.ux = d->ux;
+      k.uy = d->uy;
+      k.t = d->t;
+    } else {
+      lbm_status s = ensure_tmp(ctx, 4 * cells);
+      if (s != LBM_OK) return s;
+      const double* src[4] = {d->n, d->ux, d->uy, d->t};
+      for (int a = 0; a < 4; ++a)
+        CK(cudaMemcpyAsync(ctx->tmp + a * cells, src[a], sizeof(double) * cells, cudaMemcpyHostToDevice, ctx->stream));
+      k.n = ctx->tmp;
+      k.ux = ctx->tmp + cells;
+      k.uy = ctx->tmp + 2 * cells;
+      k.t = ctx->tmp + 3 * cells;
+    }
+  } else {
+    return fail(ctx, LBM_EINVAL, "lbm_init_riemann: bad kind");
+  }
+  switch (ctx->prec) {
+    case LBM_F64: launch_init_t<double>(ctx, P, k); break;
+    case LBM_F32_DEV: launch_init_t<float>(ctx, P, k); break;
+    default: launch_init_t<__nv_bfloat16>(ctx, P, k); break;
+  }
+  CKL();
+  ctx->launches += 1;
+  if (d->kind == LBM_INIT_FIELD && !d->field_on_device) CK(cudaStreamSynchronize(ctx->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps) {
+  if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_step: NULL context");
+  if (nsteps < 0) return fail(ctx, LBM_EINVAL, "lbm_step: nsteps < 0");
+  while (nsteps >= kGraphChunk) {
+    cudaGraphExec_t& ge = ctx->graph[ctx->cur];
+    if (!ge) {
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal));
+      int c = ctx->cur;
+      for (int s = 0; s < kGraphChunk; ++s) {
+        launch_step(ctx, ctx->buf[c], ctx->buf[c ^ 1], ctx->cap);
+        c ^= 1;
+      }
+      cudaError_t le = cudaGetLastError();
+      cudaError_t ee = cudaStreamEndCapture(ctx->cap, &g);
+      if (le != cudaSuccess || ee != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(ctx, LBM_ECUDA, std::string("lbm_step: capture: ") + cudaGetErrorString(le != cudaSuccess ? le : ee));
+      }
+      cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) {
+        ge = nullptr;
+        return fail(ctx, LBM_ECUDA, std::string("lbm_step: instantiate: ") + cudaGetErrorString(ie));
+      }
+    }
+    CK(cudaGraphLaunch(ge, ctx->stream));
+    ctx->launches += kGraphChunk;
+    nsteps -= kGraphChunk;
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    launch_step(ctx, ctx->buf[ctx->cur], ctx->buf[ctx->cur ^ 1], ctx->stream);
+    CKL();
+    ctx->cur ^= 1;
+    ctx->launches += 1;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_ctx* ctx, int32_t problem, double* n, double* ux, double* uy, double* T, double* mu,
+                       double* t, int32_t out_on_device, lbm_diag* diag) {
+  if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_moments: NULL context");
+  if (problem < 0 || problem >= ctx->nprob) return fail(ctx, LBM_EINVAL, "lbm_moments: bad problem index");
+  const ProbDev& P = ctx->ph[problem];
+  const int64_t cells = (int64_t)P.nx * P.ny;
+  const unsigned g = blocks_for(cells, kMomThreads);
+  if (ctx->partials_cap < (int64_t)g * kNPartial) {
+    if (ctx->partials) CK(cudaFree(ctx->partials));
+    ctx->partials = nullptr;
+    ctx->partials_cap = 0;
+    CK(cudaMalloc(&ctx->partials, sizeof(double) * kNPartial * g));
+    ctx->partials_cap = (int64_t)g * kNPartial;
+  }
+  double* user[6] = {n, ux, uy, T, mu, t};
+  double* o[6] = {n, ux, uy, T, mu, t};
+  if (!out_on_device) {
+    int nf = 0;
+    for (int a = 0; a < 6; ++a) nf += user[a] != nullptr;
+    lbm_status s = ensure_tmp(ctx, nf * cells);
+    if (s != LBM_OK) return s;
+    int k = 0;
+    for (int a = 0; a < 6; ++a) o[a] = user[a] ? ctx->tmp + (k++) * cells : nullptr;
+  }
+  switch (ctx->prec) {
+    case LBM_F64: launch_moments_p<double>(ctx, P, o, g); break;
+    case LBM_F32_DEV: launch_moments_p<float>(ctx, P, o, g); break;
+    default: launch_moments_p<__nv_bfloat16>(ctx, P, o, g); break;
+  }
+  CKL();
+  ctx->launches += 1;
+  if (diag) {
+    reduce_partials_kernel<<<1, 256, 0, ctx->stream>>>(ctx->partials, g, ctx->diag_d);
+    CKL();
+    ctx->launches += 1;
+  }
+  if (!out_on_device) {
+    for (int a = 0; a < 6; ++a)
+      if (user[a]) CK(cudaMemcpyAsync(user[a], o[a], sizeof(double) * cells, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  if (diag) {
+    double h[kNPartial];
+    CK(cudaMemcpyAsync(h, ctx->diag_d, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    diag->sum_n = h[0];
+    diag->sum_jx = h[1];
+    diag->sum_jy = h[2];
+    diag->sum_E = h[3];
+    diag->clamped = (int64_t)h[4];
+    diag->nonfinite = (int64_t)h[5];
+  } else if (!out_on_device) {
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx* ctx, int32_t problem, double* f, int32_t on_device) {
+  if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_get_populations: NULL context");
+  if (problem < 0 || problem >= ctx->nprob || !f) return fail(ctx, LBM_EINVAL, "lbm_get_populations: bad argument");
+  const ProbDev& P = ctx->ph[problem];
+  const int64_t cells = (int64_t)P.nx * P.ny;
+  double* dst = f;
+  if (!on_device) {
+    lbm_status s = ensure_tmp(ctx, 9 * cells);
+    if (s != LBM_OK) return s;
+    dst = ctx->tmp;
+  }
+  const unsigned g = blocks_for(cells, 256);
+  switch (ctx->prec) {
+    case LBM_F64: get_pop_kernel<double><<<g, 256, 0, ctx->stream>>>((const double*)ctx->buf[ctx->cur], P, ctx->plane, dst); break;
+    case LBM_F32_DEV: get_pop_kernel<float><<<g, 256, 0, ctx->stream>>>((const float*)ctx->buf[ctx->cur], P, ctx->plane, dst); break;
+    default: get_pop_kernel<__nv_bfloat16><<<g, 256, 0, ctx->stream>>>((const __nv_bfloat16*)ctx->buf[ctx->cur], P, ctx->plane, dst); break;
+  }
+  CKL();
+  ctx->launches += 1;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(f, dst, sizeof(double) * 9 * cells, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_ctx* ctx, int32_t problem, const double* f, int32_t on_device) {
+  if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_set_populations: NULL context");
+  if (problem < 0 || problem >= ctx->nprob || !f) return fail(ctx, LBM_EINVAL, "lbm_set_populations: bad argument");
+  const ProbDev& P = ctx->ph[problem];
+  const int64_t cells = (int64_t)P.nx * P.ny;
+  const double* src = f;
+  if (!on_device) {
+    lbm_status s = ensure_tmp(ctx, 9 * cells);
+    if (s != LBM_OK) return s;
+    CK(cudaMemcpyAsync(ctx->tmp, f, sizeof(double) * 9 * cells, cudaMemcpyHostToDevice, ctx->stream));
+    src = ctx->tmp;
+  }
+  const unsigned g = blocks_for(cells, 256);
+  switch (ctx->prec) {
+    case LBM_F64: set_pop_kernel<double><<<g, 256, 0, ctx->stream>>>((double*)ctx->buf[ctx->cur], P, ctx->plane, src); break;
+    case LBM_F32_DEV: set_pop_kernel<float><<<g, 256, 0, ctx->stream>>>((float*)ctx->buf[ctx->cur], P, ctx->plane, src); break;
+    default: set_pop_kernel<__nv_bfloat16><<<g, 256, 0, ctx->stream>>>((__nv_bfloat16*)ctx->buf[ctx->cur], P, ctx->plane, src); break;
+  }
+  CKL();
+  ctx->launches += 1;
+  if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_ctx* ctx) {
+  if (!ctx) return LBM_OK;
+  cudaStreamSynchronize(ctx->stream);
+  for (int b = 0; b < 2; ++b) {
+    if (ctx->graph[b]) cudaGraphExecDestroy(ctx->graph[b]);
+    if (ctx->buf[b]) cudaFree(ctx->buf[b]);
+  }
+  if (ctx->pd) cudaFree(ctx->pd);
+  if (ctx->lim_d) cudaFree(ctx->lim_d);
+  if (ctx->diag_d) cudaFree(ctx->diag_d);
+  if (ctx->partials) cudaFree(ctx->partials);
+  if (ctx->tmp) cudaFree(ctx->tmp);
+  if (ctx->cap) cudaStreamDestroy(ctx->cap);
+  delete ctx;
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,385 @@
+// Kernels of the d2v9 generalized-polynomial LBGK step (sm_103a).
+//
+// Layout in HBM: structure of arrays, one plane per velocity a = 0..8 of
+// `plane` cells; problem p occupies cells [base_p, base_p + ny_p * pitch_p)
+// of every plane, row-major with a row pitch rounded up to 32 cells.  Two
+// such buffers alternate (read A, write B).  Velocity order: rest; (1,0),
+// (0,1), (-1,0), (0,-1); (1,1), (-1,1), (-1,-1), (1,-1).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fd_device.cuh"
+
+namespace lbm {
+
+enum { STAT_FD = 0, STAT_T0 = 1, STAT_MB = 2 };
+enum { BC_PERIODIC = 0, BC_BOUNCEBACK = 1 };
+
+constexpr int kTileX = 128;  // cells of one row handled by one CTA (one per thread)
+
+struct ProbDev {
+  int32_t nx, ny, pitch, bc_x, bc_y, tiles_x;
+  int64_t base, tile_begin;
+  double tau, omega;
+  double n_ref, t_ref;               // deviation reference state (n_ref = 0: absolute storage)
+  double j2_ref, ndelta_ref;         // J_2(t_ref), n_ref (3/2 - J_2(t_ref))
+  double wref[9];                    // W_a^ref = w_a(J_2(t_ref)) n_ref
+  struct {
+    float omega, n_ref, ndelta_ref;
+    float wref[3];  // rest, short, long
+  } f;              // FP32 copies for the reduced-precision step
+};
+
+// Closure constants of the statistics without inversion.
+template <int STAT>
+struct FixedJ {
+  static constexpr double j2 = STAT == STAT_T0 ? 1.5 : 1.0;  // 1 + 2/(2 + D) | 1
+  static constexpr double j4 = STAT == STAT_T0 ? 4.0 / 3.0 : 1.0;
+};
+
+// Locate the problem and the (row, x-tile) of this CTA.
+__device__ __forceinline__ int find_problem(const ProbDev* __restrict__ probs, int nprob, int64_t tile) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].tile_begin <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// K = 3 equilibrium in geometric velocities (Sect. "The Gaussian quadrature",
+// D = 2), FP64.  W_0 = n(1 - 5J_2/9), W_short = nJ_2/9, W_long = nJ_2/36.
+__device__ __forceinline__ void feq_f64(double n, double ux, double uy, double J2, double J4, double fe[9]) {
+  const double u2 = ux * ux + uy * uy;
+  const double D22 = 1.0 / (2.0 - J2);        // 2/((D+2) - J_2 D)
+  const double D42 = 1.0 / (3.0 - 2.0 * J4);  // 2/((D+4) - J_4 (D+2))
+  const double iJ2 = 1.0 / J2;
+  const double a1 = 3.0 * iJ2, a2 = 4.5 * iJ2, b0 = 1.5 * iJ2;
+  const double a3 = 2.25 * (D22 - 1.0) * iJ2;  // (9/2)(D22-1)/(J2 D)
+  const double a4 = 1.5 * D22;
+  const double k0 = 4.0 * (1.0 - J2) * J4 * D42;  // (1-J2) J4 (D+2) D42
+  const double k1 = 3.0 * (1.0 - J2) * J4 * D42;
+  const double k2 = 3.0 * J4 * D42;
+  const double k3 = 2.25 * J4 * (D42 - 1.0);  // 9 J4 (D42-1)/(D+2)
+  const double k4 = 3.0 * J4;
+  const double W0 = n * (1.0 - 5.0 * J2 / 9.0), Ws = n * J2 / 9.0, Wl = n * J2 / 36.0;
+  // class constants: e2 = 0 (rest), 1 (short), 2 (long)
+  const double C1 = k0 - k1 + (k3 - k2) * u2, C2 = k0 - 2.0 * k1 + (2.0 * k3 - k2) * u2;
+  const double Q0 = -a4 * u2, Q1 = (a3 - a4) * u2, Q2 = (2.0 * a3 - a4) * u2;
+  auto S = [&](double eu, double C, double Qc) {
+    return 1.0 + Qc + eu * (a1 + a2 * eu + b0 * (C + k4 * eu * eu));
+  };
+  fe[0] = W0 * (1.0 + Q0);
+  fe[1] = Ws * S(ux, C1, Q1);
+  fe[2] = Ws * S(uy, C1, Q1);
+  fe[3] = Ws * S(-ux, C1, Q1);
+  fe[4] = Ws * S(-uy, C1, Q1);
+  fe[5] = Wl * S(ux + uy, C2, Q2);
+  fe[6] = Wl * S(-ux + uy, C2, Q2);
+  fe[7] = Wl * S(-ux - uy, C2, Q2);
+  fe[8] = Wl * S(ux - uy, C2, Q2);
+}
+
+// J_2, J_4 of a state given by t (FD) or by the closure.
+template <int STAT>
+__device__ __forceinline__ void closure_from_t(double t, double& J2, double& J4) {
+  if (STAT == STAT_FD) {
+    const FD5 f = fd_eval(x_of_t(t));
+    J2 = j2_of(f);
+    J4 = j4_of(f);
+  } else {
+    J2 = FixedJ<STAT>::j2;
+    J4 = FixedJ<STAT>::j4;
+  }
+}
+
+// Pull indices of the nine populations of cell (x, y); a negative row or
+// column marks an off-lattice source (bounce-back from the opposite
+// population of the same cell).
+struct PullIdx {
+  int64_t row, rm, rp;  // rows y, y-1, y+1 (base included), -1 if off-lattice
+  int xm, xp;           // columns x-1, x+1, -1 if off-lattice
+};
+
+__device__ __forceinline__ PullIdx pull_index(const ProbDev& P, int x, int y) {
+  PullIdx q;
+  q.row = P.base + (int64_t)y * P.pitch;
+  const int ym = y > 0 ? y - 1 : (P.bc_y == BC_PERIODIC ? P.ny - 1 : -1);
+  const int yp = y < P.ny - 1 ? y + 1 : (P.bc_y == BC_PERIODIC ? 0 : -1);
+  q.rm = ym >= 0 ? P.base + (int64_t)ym * P.pitch : -1;
+  q.rp = yp >= 0 ? P.base + (int64_t)yp * P.pitch : -1;
+  q.xm = x > 0 ? x - 1 : (P.bc_x == BC_PERIODIC ? P.nx - 1 : -1);
+  q.xp = x < P.nx - 1 ? x + 1 : (P.bc_x == BC_PERIODIC ? 0 : -1);
+  return q;
+}
+
+template <class T>
+__device__ __forceinline__ void pull9(const T* __restrict__ fin, int64_t plane, const PullIdx& q, int x, T v[9]) {
+  auto ld = [&](int a, int64_t r, int xs, int opp) -> T {
+    return (r < 0 || xs < 0) ? fin[opp * plane + q.row + x] : fin[a * plane + r + xs];
+  };
+  v[0] = fin[q.row + x];
+  v[1] = ld(1, q.row, q.xm, 3);
+  v[2] = ld(2, q.rm, x, 4);
+  v[3] = ld(3, q.row, q.xp, 1);
+  v[4] = ld(4, q.rp, x, 2);
+  v[5] = ld(5, q.rm, q.xm, 7);
+  v[6] = ld(6, q.rm, q.xp, 8);
+  v[7] = ld(7, q.rp, q.xp, 5);
+  v[8] = ld(8, q.rp, q.xm, 6);
+}
+
+// ------------------------------------------------------------------ FP64 step
+
+template <int STAT>
+__global__ void __launch_bounds__(kTileX) stream_collide_f64(const double* __restrict__ fin, double* __restrict__ fout,
+                                                             const ProbDev* __restrict__ probs, int nprob,
+                                                             int64_t plane, InvLimits L) {
+  const int64_t tile = blockIdx.x;
+  const int p = nprob == 1 ? 0 : find_problem(probs, nprob, tile);
+  const ProbDev& P = probs[p];
+  const int64_t lt = tile - P.tile_begin;
+  const int y = (int)(lt / P.tiles_x);
+  const int x = (int)(lt % P.tiles_x) * kTileX + threadIdx.x;
+  if (x >= P.nx) return;
+  const PullIdx q = pull_index(P, x, y);
+  double f[9];
+  pull9(fin, plane, q, x, f);
+
+  // moments (the moment update after the LBGK equation, plus the energy)
+  const double n = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  const double jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+  const double jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+  const double E = ((f[1] + f[2]) + (f[3] + f[4])) + 2.0 * ((f[5] + f[6]) + (f[7] + f[8]));
+  const double in = 1.0 / n;
+  const double ux = jx * in, uy = jy * in;
+  double J2, J4;
+  if (STAT == STAT_FD) {
+    J2 = 1.5 * (E * in - (ux * ux + uy * uy));  // 3 (E/n - u^2)/D
+    int cl;
+    const double xx = invert_j2(J2, L, &cl);
+    J4 = j4_of(fd_eval(xx));
+  } else {
+    J2 = FixedJ<STAT>::j2;
+    J4 = FixedJ<STAT>::j4;
+  }
+  double fe[9];
+  feq_f64(n, ux, uy, J2, J4, fe);
+  const double w = P.omega;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) fout[a * plane + q.row + x] = fma(w, fe[a] - f[a], f[a]);
+}
+
+// ------------------------------------------------------------------ per-context setup
+
+__global__ void setup_kernel(InvLimits* out) {
+  InvLimits L;
+  L.x_lo = x_of_t(kTMax);
+  L.x_hi = x_of_t(kTMin);
+  L.j2_lo = j2_of(fd_eval(L.x_lo));
+  L.j2_hi = j2_of(fd_eval(L.x_hi));
+  *out = L;
+}
+
+// Deviation reference of each problem: J_2,ref from t_ref (or the closure's
+// constant), W^ref = w_a(J_2,ref) n_ref and n_ref (3/2 - J_2,ref).
+__global__ void ref_kernel(ProbDev* probs, int nprob, int stat) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nprob) return;
+  ProbDev& P = probs[p];
+  double J2, J4;
+  if (stat == STAT_FD) {
+    if (P.n_ref > 0.0) closure_from_t<STAT_FD>(P.t_ref, J2, J4); else J2 = 1.5;
+  } else if (stat == STAT_T0) {
+    J2 = FixedJ<STAT_T0>::j2;
+  } else {
+    J2 = FixedJ<STAT_MB>::j2;
+  }
+  const double n = P.n_ref;
+  const double w0 = n * (1.0 - 5.0 * J2 / 9.0), ws = n * J2 / 9.0, wl = n * J2 / 36.0;
+  P.j2_ref = J2;
+  P.ndelta_ref = n * (1.5 - J2);
+  P.wref[0] = w0;
+  for (int a = 1; a <= 4; ++a) P.wref[a] = ws;
+  for (int a = 5; a <= 8; ++a) P.wref[a] = wl;
+  P.f.omega = (float)P.omega;
+  P.f.n_ref = (float)n;
+  P.f.ndelta_ref = (float)P.ndelta_ref;
+  P.f.wref[0] = (float)w0;
+  P.f.wref[1] = (float)ws;
+  P.f.wref[2] = (float)wl;
+}
+
+// ------------------------------------------------------------------ storage traits
+
+template <class T>
+struct Stor;
+template <>
+struct Stor<double> {
+  static constexpr bool dev = false;
+  __device__ static double to_f64(double v, double) { return v; }
+  __device__ static double from_f64(double f, double) { return f; }
+};
+template <>
+struct Stor<float> {
+  static constexpr bool dev = true;
+  __device__ static double to_f64(float v, double w) { return w + (double)v; }
+  __device__ static float from_f64(double f, double w) { return (float)(f - w); }
+};
+template <>
+struct Stor<__nv_bfloat16> {
+  static constexpr bool dev = true;
+  __device__ static double to_f64(__nv_bfloat16 v, double w) { return w + (double)__bfloat162float(v); }
+  __device__ static __nv_bfloat16 from_f64(double f, double w) { return __float2bfloat16_rn((float)(f - w)); }
+};
+
+// ------------------------------------------------------------------ init
+
+struct InitDesc {
+  int32_t kind, x0, y0;
+  double s[4][4];  // n, ux, uy, t of up to four regions
+  const double *n, *ux, *uy, *t;  // device arrays for FIELD
+};
+
+template <class T, int STAT>
+__global__ void init_kernel(T* __restrict__ f, ProbDev P, int64_t plane, InitDesc d) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t cells = (int64_t)P.nx * P.ny;
+  if (i >= cells) return;
+  const int y = (int)(i / P.nx), x = (int)(i % P.nx);
+  double n, ux, uy, t;
+  if (d.kind == 2) {
+    n = d.n[i]; ux = d.ux[i]; uy = d.uy[i]; t = d.t[i];
+  } else {
+    const int r = d.kind == 0 ? (x >= d.x0) : (x >= d.x0) + 2 * (y >= d.y0);
+    n = d.s[r][0]; ux = d.s[r][1]; uy = d.s[r][2]; t = d.s[r][3];
+  }
+  double J2, J4;
+  closure_from_t<STAT>(t, J2, J4);
+  double fe[9];
+  feq_f64(n, ux, uy, J2, J4, fe);
+  const int64_t c = P.base + (int64_t)y * P.pitch + x;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) f[a * plane + c] = Stor<T>::from_f64(fe[a], Stor<T>::dev ? P.wref[a] : 0.0);
+}
+
+// ------------------------------------------------------------------ populations in / out
+
+template <class T>
+__global__ void get_pop_kernel(const T* __restrict__ f, ProbDev P, int64_t plane, double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t cells = (int64_t)P.nx * P.ny;
+  if (i >= cells) return;
+  const int y = (int)(i / P.nx), x = (int)(i % P.nx);
+  const int64_t c = P.base + (int64_t)y * P.pitch + x;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) out[a * cells + i] = Stor<T>::to_f64(f[a * plane + c], Stor<T>::dev ? P.wref[a] : 0.0);
+}
+
+template <class T>
+__global__ void set_pop_kernel(T* __restrict__ f, ProbDev P, int64_t plane, const double* __restrict__ in) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t cells = (int64_t)P.nx * P.ny;
+  if (i >= cells) return;
+  const int y = (int)(i / P.nx), x = (int)(i % P.nx);
+  const int64_t c = P.base + (int64_t)y * P.pitch + x;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) f[a * plane + c] = Stor<T>::from_f64(in[a * cells + i], Stor<T>::dev ? P.wref[a] : 0.0);
+}
+
+// ------------------------------------------------------------------ moments
+
+constexpr int kMomThreads = 256;
+constexpr int kNPartial = 6;  // sum n, jx, jy, E, clamped, nonfinite
+
+template <class T, int STAT>
+__global__ void __launch_bounds__(kMomThreads) moments_kernel(const T* __restrict__ f, ProbDev P, int64_t plane,
+                                                              InvLimits L, double* __restrict__ on,
+                                                              double* __restrict__ oux, double* __restrict__ ouy,
+                                                              double* __restrict__ oT, double* __restrict__ omu,
+                                                              double* __restrict__ ot, double* __restrict__ partials) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t cells = (int64_t)P.nx * P.ny;
+  double acc[kNPartial] = {0, 0, 0, 0, 0, 0};
+  if (i < cells) {
+    const int y = (int)(i / P.nx), x = (int)(i % P.nx);
+    const int64_t c = P.base + (int64_t)y * P.pitch + x;
+    double v[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) v[a] = Stor<T>::to_f64(f[a * plane + c], Stor<T>::dev ? P.wref[a] : 0.0);
+    const double n = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+    const double jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
+    const double jy = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
+    const double E = ((v[1] + v[2]) + (v[3] + v[4])) + 2.0 * ((v[5] + v[6]) + (v[7] + v[8]));
+    const double ux = jx / n, uy = jy / n;
+    double theta = 0.0, mu = 0.0, t = 0.0;
+    int cl = 0;
+    if (STAT == STAT_FD) {
+      const double J2 = 1.5 * (E / n - (ux * ux + uy * uy));
+      const double xx = invert_j2(J2, L, &cl);
+      const FD5 F = fd_eval(xx);
+      t = 1.0 / F.f1;                  // t = T/T_F = 1/f_1(x)
+      theta = n * t / (2.0 * kPi);     // theta = n t/(2 pi), T_F = n/(2 pi)
+      mu = theta * xx;
+    } else if (STAT == STAT_T0) {
+      theta = 0.0; t = 0.0; mu = n / (2.0 * kPi);
+    } else {
+      theta = mu = t = __longlong_as_double(0x7ff8000000000000LL);
+    }
+    if (on) on[i] = n;
+    if (oux) oux[i] = ux;
+    if (ouy) ouy[i] = uy;
+    if (oT) oT[i] = theta;
+    if (omu) omu[i] = mu;
+    if (ot) ot[i] = t;
+    acc[0] = n; acc[1] = jx; acc[2] = jy; acc[3] = E;
+    acc[4] = cl;
+    bool fin = isfinite(n) && isfinite(jx) && isfinite(jy) && isfinite(E);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) fin = fin && isfinite(v[a]);
+    acc[5] = fin ? 0.0 : 1.0;
+  }
+  // fixed-order block reduction: warp shuffle tree, then warps in order
+  __shared__ double sh[kMomThreads / 32][kNPartial];
+#pragma unroll
+  for (int k = 0; k < kNPartial; ++k) {
+    double s = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    acc[k] = s;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < kNPartial; ++k) sh[wid][k] = acc[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < kNPartial) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kMomThreads / 32; ++w) s += sh[w][threadIdx.x];
+    partials[(int64_t)blockIdx.x * kNPartial + threadIdx.x] = s;
+  }
+}
+
+// One block sums the per-block partials in a fixed order.
+__global__ void __launch_bounds__(256) reduce_partials_kernel(const double* __restrict__ partials, int64_t nblocks,
+                                                              double* __restrict__ out) {
+  __shared__ double sh[256];
+  for (int k = 0; k < kNPartial; ++k) {
+    double s = 0.0;
+    for (int64_t b = threadIdx.x; b < nblocks; b += 256) s += partials[b * kNPartial + k];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = sh[0];
+    __syncthreads();
+  }
+}
+
+}  // namespace lbm

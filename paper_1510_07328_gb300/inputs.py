@@ -208,3 +208,23 @@ def surrogate_set(count: int, seed: int = 4, n_lo: float = 0.5, n_hi: float = 2.
     n = n_lo + (n_hi - n_lo) * r[:count]
     t = np.exp(math.log(t_lo) + (math.log(t_hi) - math.log(t_lo)) * r[count:])
     return n, t
+
+
+def random_field(nx: int, ny: int, seed: int, tau: float = 0.7, bc_x: str = "periodic",
+                 bc_y: str = "periodic", n_lo: float = 0.7, n_hi: float = 1.2, u_max: float = 0.1,
+                 t_lo: float = 0.02, t_hi: float = 0.3) -> Problem:
+    """Per-cell random state: n ~ U[n_lo, n_hi], u0 ~ U[-u_max, u_max]^2,
+    t ~ U[t_lo, t_hi] (test inputs spanning several tiles and ragged edges)."""
+    c = nx * ny
+    r = uniform(seed, 4 * c)
+    n = (n_lo + (n_hi - n_lo) * r[:c]).reshape(ny, nx)
+    ux = (u_max * (2 * r[c:2 * c] - 1)).reshape(ny, nx)
+    uy = (u_max * (2 * r[2 * c:3 * c] - 1)).reshape(ny, nx)
+    t = (t_lo + (t_hi - t_lo) * r[3 * c:]).reshape(ny, nx)
+    return Problem(nx, ny, tau, bc_x, bc_y, n, ux, uy, t, name=f"random_{nx}x{ny}", kind="field")
+
+
+def perturb_populations(f: np.ndarray, seed: int, amp: float) -> np.ndarray:
+    """Multiply populations by (1 + amp * U[-1, 1]) to leave equilibrium."""
+    r = uniform(seed, f.size).reshape(f.shape)
+    return f * (1.0 + amp * (2.0 * r - 1.0))

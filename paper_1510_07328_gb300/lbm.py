@@ -1,0 +1,239 @@
+"""Thin ctypes binding of the C ABI in include/lbm.h.
+
+Every function here only marshals arguments and calls the library of the same
+name; all arithmetic of the method runs in the CUDA kernels of
+``liblbm_gb300.so``.  Importing this module loads the library and fails loudly
+if it has not been built (``python -m paper_1510_07328_gb300.build``); there is
+no CPU fallback.
+
+Device buffers and streams come from PyTorch (``torch.cuda`` tensors and
+``torch.cuda.current_stream().cuda_stream``); host buffers are NumPy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ETIMEOUT, LBM_EUNSUPPORTED = range(6)
+LBM_STAT_FD, LBM_STAT_FD_T0, LBM_STAT_MB = range(3)
+LBM_F64, LBM_F32_DEV, LBM_BF16_DEV = range(3)
+LBM_INV_EXACT, LBM_INV_SURROGATE = range(2)
+LBM_BC_PERIODIC, LBM_BC_BOUNCEBACK = range(2)
+LBM_INIT_HALF, LBM_INIT_QUADRANT, LBM_INIT_FIELD = range(3)
+
+STAT = {"fd": LBM_STAT_FD, "t0": LBM_STAT_FD_T0, "mb": LBM_STAT_MB}
+PREC = {"f64": LBM_F64, "f32": LBM_F32_DEV, "bf16": LBM_BF16_DEV}
+BC = {"periodic": LBM_BC_PERIODIC, "bounceback": LBM_BC_BOUNCEBACK}
+
+
+class lbm_problem(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("tau", C.c_double), ("bc_x", C.c_int32),
+                ("bc_y", C.c_int32), ("n_ref", C.c_double), ("t_ref", C.c_double)]
+
+
+class lbm_params(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("order", C.c_int32), ("stat", C.c_int32), ("prec", C.c_int32),
+                ("inv", C.c_int32), ("nproblems", C.c_int32), ("problems", C.POINTER(lbm_problem))]
+
+
+class lbm_state(C.Structure):
+    _fields_ = [("n", C.c_double), ("ux", C.c_double), ("uy", C.c_double), ("t", C.c_double)]
+
+
+class lbm_riemann_desc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("x0", C.c_int32), ("y0", C.c_int32), ("s", lbm_state * 4),
+                ("n", C.c_void_p), ("ux", C.c_void_p), ("uy", C.c_void_p), ("t", C.c_void_p),
+                ("field_on_device", C.c_int32)]
+
+
+class lbm_diag(C.Structure):
+    _fields_ = [("sum_n", C.c_double), ("sum_jx", C.c_double), ("sum_jy", C.c_double), ("sum_E", C.c_double),
+                ("clamped", C.c_int64), ("nonfinite", C.c_int64)]
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_1510_07328_gb300.build` "
+                          "(the library has no CPU fallback)")
+    lib = C.CDLL(path)
+    V = C.c_void_p
+    sig = {
+        "lbm_create": (C.c_int, [C.POINTER(lbm_params), V, C.POINTER(V)]),
+        "lbm_init_riemann": (C.c_int, [V, C.c_int32, C.POINTER(lbm_riemann_desc)]),
+        "lbm_step": (C.c_int, [V, C.c_int32]),
+        "lbm_moments": (C.c_int, [V, C.c_int32, V, V, V, V, V, V, C.c_int32, C.POINTER(lbm_diag)]),
+        "lbm_get_populations": (C.c_int, [V, C.c_int32, V, C.c_int32]),
+        "lbm_set_populations": (C.c_int, [V, C.c_int32, V, C.c_int32]),
+        "lbm_destroy": (C.c_int, [V]),
+        "lbm_last_error": (C.c_char_p, [V]),
+        "lbm_launch_count": (C.c_int64, [V]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+LIB = _load()
+EXPORTS = ("lbm_create", "lbm_init_riemann", "lbm_step", "lbm_moments", "lbm_get_populations",
+           "lbm_set_populations", "lbm_destroy", "lbm_last_error", "lbm_launch_count")
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+def _check(status: int, ctx) -> None:
+    if status != LBM_OK:
+        raise LbmError(status, LIB.lbm_last_error(ctx).decode())
+
+
+def _ptr(a) -> int | None:
+    """Address of a NumPy array or torch tensor (None stays NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"] or a.dtype != np.float64:
+            raise ValueError("host arrays must be C-contiguous float64")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous() or str(a.dtype) != "torch.float64":
+            raise ValueError("device tensors must be contiguous float64")
+        return a.data_ptr()
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+# ---------------------------------------------------------------- C-ABI calls, same names
+
+
+def lbm_create(problems, stat="fd", prec="f64", inv="exact", stream=None):
+    """problems: list of dicts with nx, ny, tau, bc_x, bc_y, n_ref, t_ref."""
+    arr = (lbm_problem * len(problems))()
+    for i, p in enumerate(problems):
+        arr[i] = lbm_problem(int(p["nx"]), int(p["ny"]), float(p["tau"]), BC[p.get("bc_x", "periodic")],
+                             BC[p.get("bc_y", "periodic")], float(p.get("n_ref", 1.0)), float(p.get("t_ref", 0.05)))
+    par = lbm_params(2, 3, STAT[stat], PREC[prec], LBM_INV_EXACT if inv == "exact" else LBM_INV_SURROGATE,
+                     len(problems), arr)
+    ctx = C.c_void_p()
+    _check(LIB.lbm_create(C.byref(par), C.c_void_p(stream or 0), C.byref(ctx)), None)
+    return ctx
+
+
+def lbm_init_riemann(ctx, problem: int, kind: str, states=(), split=(0, 0), fields=None, on_device=False):
+    d = lbm_riemann_desc()
+    d.kind = {"half": LBM_INIT_HALF, "quadrant": LBM_INIT_QUADRANT, "field": LBM_INIT_FIELD}[kind]
+    d.x0, d.y0 = int(split[0]), int(split[1])
+    for r, s in enumerate(states):
+        d.s[r] = lbm_state(*[float(v) for v in s])
+    keep = []
+    if fields is not None:
+        for name in ("n", "ux", "uy", "t"):
+            a = fields[name]
+            if isinstance(a, np.ndarray):
+                a = np.ascontiguousarray(a, dtype=np.float64)
+            keep.append(a)
+            setattr(d, name, _ptr(a))
+        d.field_on_device = 1 if on_device else 0
+    _check(LIB.lbm_init_riemann(ctx, int(problem), C.byref(d)), ctx)
+
+
+def lbm_step(ctx, nsteps: int):
+    _check(LIB.lbm_step(ctx, int(nsteps)), ctx)
+
+
+def lbm_moments(ctx, problem: int, n=None, ux=None, uy=None, T=None, mu=None, t=None, on_device=False,
+                diag=False):
+    dg = lbm_diag() if diag else None
+    _check(LIB.lbm_moments(ctx, int(problem), _ptr(n), _ptr(ux), _ptr(uy), _ptr(T), _ptr(mu), _ptr(t),
+                           1 if on_device else 0, C.byref(dg) if dg is not None else None), ctx)
+    if dg is not None:
+        return {"sum_n": dg.sum_n, "sum_jx": dg.sum_jx, "sum_jy": dg.sum_jy, "sum_E": dg.sum_E,
+                "clamped": dg.clamped, "nonfinite": dg.nonfinite}
+    return None
+
+
+def lbm_get_populations(ctx, problem: int, f, on_device=False):
+    _check(LIB.lbm_get_populations(ctx, int(problem), _ptr(f), 1 if on_device else 0), ctx)
+
+
+def lbm_set_populations(ctx, problem: int, f, on_device=False):
+    _check(LIB.lbm_set_populations(ctx, int(problem), _ptr(f), 1 if on_device else 0), ctx)
+
+
+def lbm_destroy(ctx):
+    _check(LIB.lbm_destroy(ctx), None)
+
+
+def lbm_last_error(ctx=None) -> str:
+    return LIB.lbm_last_error(ctx).decode()
+
+
+def lbm_launch_count(ctx) -> int:
+    return int(LIB.lbm_launch_count(ctx))
+
+
+# ---------------------------------------------------------------- convenience
+
+
+class Lattice:
+    """One context over a list of problems (``inputs.Problem`` objects)."""
+
+    def __init__(self, problems, stat="fd", prec="f64", stream=None, t_ref=None, n_ref=None):
+        self.problems = list(problems)
+        descs = []
+        for p in self.problems:
+            tr = t_ref if t_ref is not None else float(np.median(p.t)) if stat == "fd" else 0.05
+            nr = n_ref if n_ref is not None else float(np.mean(p.n))
+            descs.append(dict(nx=p.nx, ny=p.ny, tau=p.tau, bc_x=p.bc_x, bc_y=p.bc_y, n_ref=nr,
+                              t_ref=min(max(tr, 1e-3), 10.0)))
+        self.ctx = lbm_create(descs, stat, prec, stream=stream)
+        self.stat = stat
+
+    def init(self, index=None, fields_on_device=None):
+        for i, p in enumerate(self.problems):
+            if index is not None and i != index:
+                continue
+            if p.kind in ("half", "quadrant"):
+                lbm_init_riemann(self.ctx, i, p.kind, p.states, p.split)
+            else:
+                f = fields_on_device if fields_on_device is not None else dict(n=p.n, ux=p.ux, uy=p.uy, t=p.t)
+                lbm_init_riemann(self.ctx, i, "field", fields=f, on_device=fields_on_device is not None)
+
+    def step(self, n: int):
+        lbm_step(self.ctx, n)
+
+    def populations(self, i: int = 0) -> np.ndarray:
+        p = self.problems[i]
+        f = np.empty((9, p.ny, p.nx))
+        lbm_get_populations(self.ctx, i, f)
+        return f
+
+    def set_populations(self, f: np.ndarray, i: int = 0):
+        lbm_set_populations(self.ctx, i, np.ascontiguousarray(f, dtype=np.float64))
+
+    def fields(self, i: int = 0, diag: bool = False) -> dict:
+        p = self.problems[i]
+        out = {k: np.empty((p.ny, p.nx)) for k in ("n", "ux", "uy", "T", "mu", "t")}
+        d = lbm_moments(self.ctx, i, diag=diag, **out)
+        if diag:
+            out["diag"] = d
+        return out
+
+    def close(self):
+        if self.ctx:
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,86 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every symbol that
+include/lbm.h declares, and rejects invalid arguments on the host before any
+CUDA call."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1510_07328_gb300 import build
+
+    build.build()
+    from paper_1510_07328_gb300 import lbm
+
+    return lbm
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lbm_create", "lbm_init_riemann", "lbm_step", "lbm_moments", "lbm_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib._build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (lbm_[a-z_]+)$", out, flags=re.M))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        assert hasattr(lib.LIB, n)
+
+
+@pytest.mark.parametrize("bad,msg", [
+    (dict(tau=0.5), "tau"),
+    (dict(nx=0), "nx"),
+    (dict(ny=-1), "nx"),
+])
+def test_create_rejects_bad_problem(lib, bad, msg):
+    p = dict(nx=8, ny=4, tau=0.8, bc_x="periodic", bc_y="periodic", n_ref=1.0, t_ref=0.05)
+    p.update(bad)
+    with pytest.raises(lib.LbmError) as e:
+        lib.lbm_create([p])
+    assert e.value.status == lib.LBM_EINVAL
+    assert msg in str(e.value)
+
+
+def test_create_rejects_reference_out_of_range(lib):
+    p = dict(nx=8, ny=4, tau=0.8, n_ref=1.0, t_ref=20.0)
+    with pytest.raises(lib.LbmError) as e:
+        lib.lbm_create([p], prec="f32")
+    assert e.value.status == lib.LBM_EINVAL and "t_ref" in str(e.value)
+    p["t_ref"] = 0.05
+    p["n_ref"] = -1.0
+    with pytest.raises(lib.LbmError):
+        lib.lbm_create([p], prec="bf16")
+
+
+def test_create_rejects_unsupported_and_null(lib):
+    import ctypes as C
+
+    arr = (lib.lbm_problem * 1)(lib.lbm_problem(8, 4, 0.8, 0, 0, 1.0, 0.05))
+    ctx = C.c_void_p()
+    par = lib.lbm_params(3, 3, 0, 0, 0, 1, arr)
+    assert lib.LIB.lbm_create(C.byref(par), None, C.byref(ctx)) == lib.LBM_EUNSUPPORTED
+    par = lib.lbm_params(2, 4, 0, 0, 0, 1, arr)
+    assert lib.LIB.lbm_create(C.byref(par), None, C.byref(ctx)) == lib.LBM_EUNSUPPORTED
+    assert "order" in lib.lbm_last_error(None)
+    assert lib.LIB.lbm_create(None, None, C.byref(ctx)) == lib.LBM_EINVAL
+    par = lib.lbm_params(2, 3, 7, 0, 0, 1, arr)
+    assert lib.LIB.lbm_create(C.byref(par), None, C.byref(ctx)) == lib.LBM_EINVAL
+    # calls on a NULL context fail cleanly
+    assert lib.LIB.lbm_step(None, 1) == lib.LBM_EINVAL
+    assert lib.LIB.lbm_destroy(None) == lib.LBM_OK
+    assert lib.LIB.lbm_launch_count(None) == 0
