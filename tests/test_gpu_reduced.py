@@ -1,0 +1,109 @@
+"""FP32 and BF16 deviation storage against the FP64 oracle.
+
+Per step, the oracle state f_k goes into the library as g = f - W_ref rounded
+to the storage type, takes one CUDA step and is compared with the oracle's
+f_{k+1}.  Error budget per step, in absolute terms:
+  storage rounding   u_s max|g|  (unit roundoff u_s = 2^-24 FP32, 2^-8 BF16, in and out)
+  FP32 arithmetic    ~ a few 2^-24 max|f| (moment sums, equilibrium, J_4
+                     from the FP32 inversion to ~1e-6 relative, entering
+                     only the third-order term)
+The tolerance is 8 u_s max|g| + 4e-6 max|f|.
+"""
+import numpy as np
+import pytest
+
+from oracle import lbm as olbm
+from paper_1510_07328_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+U_STORE = {"f32": 2.0 ** -24, "bf16": 2.0 ** -8}
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_1510_07328_gb300 import build
+
+    build.build()
+    from paper_1510_07328_gb300 import lbm
+
+    return lbm
+
+
+def oinit(p, stat="fd"):
+    return olbm.init_equilibrium(p.n, p.ux, p.uy, p.t, stat)
+
+
+def wref(p, stat, n_ref, t_ref):
+    """W_a^ref of the library's deviation storage, from the oracle's weights."""
+    from oracle import fd, gpoly
+
+    if stat == "fd":
+        j2 = float(fd.j2_of_x(fd.x_of_t(np.array([t_ref])))[0])
+    else:
+        j2 = 1.5 if stat == "t0" else 1.0
+    return gpoly.weights(2, n_ref, j2)
+
+
+CASES = {
+    "random_300x5_bb": lambda: inputs.random_field(300, 5, 61, tau=0.7, bc_x="bounceback"),
+    "random_129x9": lambda: inputs.random_field(129, 9, 62, tau=0.58, t_lo=0.005, t_hi=0.3),
+    "riemann_400x4": lambda: inputs.riemann_1d(),
+}
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+@pytest.mark.parametrize("stat", ["fd", "t0", "mb"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_step_parity_reduced(L, prec, stat, name):
+    p = CASES[name]()
+    n_ref, t_ref = 0.95, 0.05
+    f = inputs.perturb_populations(oinit(p, stat), 71, 0.01)
+    par = olbm.Params(tau=p.tau, bc_x=p.bc_x, bc_y=p.bc_y, stat=stat)
+    W = wref(p, stat, n_ref, t_ref)[:, None, None]
+    lat = L.Lattice([p], stat=stat, prec=prec, n_ref=n_ref, t_ref=t_ref)
+    for _ in range(2):
+        lat.set_populations(f)
+        lat.step(1)
+        got = lat.populations(0)
+        g_in = np.abs(f - W).max()
+        f = olbm.step(f, par)
+        g_out = np.abs(f - W).max()
+        tol = 8 * U_STORE[prec] * max(g_in, g_out) + 4e-6 * np.abs(f).max()
+        err = np.abs(got - f).max()
+        assert err <= tol, (err, tol)
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+def test_init_reduced(L, prec):
+    p = CASES["random_300x5_bb"]()
+    lat = L.Lattice([p], stat="fd", prec=prec, n_ref=0.95, t_ref=0.05)
+    lat.init()
+    got = lat.populations(0)
+    lat.close()
+    ref = oinit(p)
+    W = wref(p, "fd", 0.95, 0.05)[:, None, None]
+    assert np.abs(got - ref).max() <= U_STORE[prec] * np.abs(ref - W).max()
+
+
+def test_fp32_against_fp64_fields_after_20_steps(L):
+    """Stated error of the FP32 path against the FP64 GPU path after 20 steps
+    on a smooth, stable-for-20-steps state: density, velocity, temperature."""
+    p = inputs.random_field(256, 64, 81, tau=0.8, u_max=0.01, n_lo=0.95, n_hi=1.05, t_lo=0.1, t_hi=0.12)
+    a = L.Lattice([p], stat="fd", prec="f64")
+    b = L.Lattice([p], stat="fd", prec="f32", n_ref=1.0, t_ref=0.11)
+    a.init()
+    b.init()
+    a.step(20)
+    b.step(20)
+    fa, fb = a.fields(0), b.fields(0)
+    a.close()
+    b.close()
+    assert np.isfinite(fa["n"]).all() and np.isfinite(fb["n"]).all()
+    assert np.abs(fb["n"] - fa["n"]).max() < 2e-6
+    assert np.abs(fb["ux"] - fa["ux"]).max() < 2e-6
+    assert (np.abs(fb["T"] - fa["T"]) / fa["T"]).max() < 1e-3
