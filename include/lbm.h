@@ -167,6 +167,40 @@ const char* lbm_last_error(const lbm_ctx* ctx);
  * was created (graph replays count each captured kernel). */
 int64_t lbm_launch_count(const lbm_ctx* ctx);
 
+/* lbm_conservation_sums_static - the paper has no counterpart to this call;
+ * it exists for callers that cannot allocate device memory.
+ *
+ * Some callers may not call cudaMalloc at all: an application or plugin whose
+ * device memory is owned by another allocator (a framework's caching
+ * allocator or an arena sized at start-up), or a loop that must not allocate
+ * while it runs.  lbm_moments allocates its per-block partial sums on first
+ * use; this call computes the same conservation totals with its partial sums
+ * in a fixed file-scope device array instead, and allocates nothing.
+ *
+ * f:     device pointer, FP64 populations [9][ny][nx] (the layout that
+ *        lbm_get_populations writes), read only.
+ * stat:  lbm_stat; for LBM_STAT_FD the count of clamped inversions is formed
+ *        as in lbm_moments, otherwise it is 0.
+ * out:   device pointer to 6 doubles, written in stream order: sum n,
+ *        sum j_x, sum j_y, sum E, clamped count, non-finite count (the fields
+ *        of lbm_diag).
+ * cuda_stream: cudaStream_t for the launches (NULL = legacy default stream).
+ *
+ * Limit: nx * ny <= LBM_STATIC_SUMS_MAX_CELLS (16,777,216 cells, a 4096 x 4096
+ * lattice); larger sizes return LBM_EINVAL before any GPU work.  The scratch
+ * array (192 KiB) lives on every GPU that loads the library until the process
+ * exits.  The first call on each device looks up the array's device address
+ * with cudaGetSymbolAddress and runs a one-thread set-up kernel, synchronising
+ * the stream; make that first call before any stream capture.  All calls
+ * share the array: calls whose kernels may overlap on the GPU (different
+ * streams or host threads) race and must be serialised by the caller.
+ * Asynchronous after the first call.  Errors: LBM_EINVAL (NULL pointer,
+ * nx or ny < 1, size above the limit, bad stat), LBM_EUNSUPPORTED (device
+ * index >= 64), LBM_ECUDA (set-up or launch failed).  No message is stored. */
+#define LBM_STATIC_SUMS_MAX_CELLS 16777216
+lbm_status lbm_conservation_sums_static(const double* f, int32_t nx, int32_t ny, int32_t stat, double* out,
+                                        void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

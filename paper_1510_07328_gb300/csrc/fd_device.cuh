@@ -55,7 +55,7 @@ __device__ __forceinline__ void fd_poly(double x, double& p2, double& p3, double
 }
 
 // S_2, S_3, S_4 at y = e^{-a}, a >= 0.
-__device__ __noinline__ void fd_alt_series(double a, double& s2, double& s3, double& s4) {
+static __device__ __noinline__ void fd_alt_series(double a, double& s2, double& s3, double& s4) {
   const double y = exp(-a);
   s2 = s3 = s4 = 0.0;
   if (a >= 2.0) {
@@ -130,7 +130,7 @@ __device__ __forceinline__ double j4_of(const FD5& f) { return f.f3 * f.f3 / (f.
 
 // Solve J_2^FD(x) = J2.  *clamped is set when x hits an end of the interval.
 // A non-finite J2 returns NaN without iterating.
-__device__ __noinline__ double invert_j2(double J2, const InvLimits& L, int* clamped) {
+static __device__ __noinline__ double invert_j2(double J2, const InvLimits& L, int* clamped) {
   *clamped = 0;
   if (!(J2 == J2) || isinf(J2)) return J2 - J2;  // NaN
   if (J2 >= L.j2_hi) {

@@ -72,6 +72,7 @@ def _load():
         "lbm_destroy": (C.c_int, [V]),
         "lbm_last_error": (C.c_char_p, [V]),
         "lbm_launch_count": (C.c_int64, [V]),
+        "lbm_conservation_sums_static": (C.c_int, [V, C.c_int32, C.c_int32, C.c_int32, V, V]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -82,7 +83,8 @@ def _load():
 
 LIB = _load()
 EXPORTS = ("lbm_create", "lbm_init_riemann", "lbm_step", "lbm_moments", "lbm_get_populations",
-           "lbm_set_populations", "lbm_destroy", "lbm_last_error", "lbm_launch_count")
+           "lbm_set_populations", "lbm_destroy", "lbm_last_error", "lbm_launch_count",
+           "lbm_conservation_sums_static")
 
 
 class LbmError(RuntimeError):
@@ -178,6 +180,14 @@ def lbm_last_error(ctx=None) -> str:
 
 def lbm_launch_count(ctx) -> int:
     return int(LIB.lbm_launch_count(ctx))
+
+
+def lbm_conservation_sums_static(f, nx: int, ny: int, out, stat="fd", stream=None):
+    """Conservation totals of device FP64 populations f[9][ny][nx] into the
+    device array out (6 doubles), without any device allocation: for callers
+    that may not call cudaMalloc.  Returns the status code (0 = LBM_OK)."""
+    return int(LIB.lbm_conservation_sums_static(C.c_void_p(_ptr(f)), int(nx), int(ny), STAT[stat],
+                                                C.c_void_p(_ptr(out)), C.c_void_p(stream or 0)))
 
 
 # ---------------------------------------------------------------- convenience
