@@ -41,6 +41,7 @@ struct lbm_ctx {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   InvLimits lim{};
+  InvLimitsF limf{};
   InvLimits* lim_d = nullptr;
   double* partials = nullptr;
   int64_t partials_cap = 0;
@@ -86,11 +87,11 @@ void launch_step_stat(lbm_ctx* c, const void* in, void* out, cudaStream_t s) {
       break;
     case LBM_F32_DEV:
       stream_collide_dev<float, STAT><<<g, kTileX, 0, s>>>((const float*)in, (float*)out, c->pd, c->nprob, c->plane,
-                                                             c->lim);
+                                                             c->lim, c->limf);
       break;
     default:
       stream_collide_dev<__nv_bfloat16, STAT><<<g, kTileX, 0, s>>>((const __nv_bfloat16*)in, (__nv_bfloat16*)out,
-                                                                     c->pd, c->nprob, c->plane, c->lim);
+                                                                     c->pd, c->nprob, c->plane, c->lim, c->limf);
       break;
   }
 }
@@ -204,14 +205,14 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
     d.n_ref = p->prec == LBM_F64 ? 0.0 : q.n_ref;
     d.t_ref = p->prec == LBM_F64 ? 0.0 : q.t_ref;
     base += (int64_t)d.pitch * q.ny;
-    tiles += (int64_t)d.tiles_x * q.ny;
+    tiles += (int64_t)d.tiles_x * ((q.ny + kTileY - 1) / kTileY);
     ctx->ph.push_back(d);
   }
   ctx->plane = (base + 31) / 32 * 32;
   ctx->ntiles = tiles;
-  if (tiles > 0x7fffffffLL) {
+  if (tiles > 0x7fffffffLL || ctx->plane > 0x7fffffffLL) {
     delete ctx;
-    return fail(nullptr, LBM_EINVAL, "lbm_create: lattice too large for one launch");
+    return fail(nullptr, LBM_EINVAL, "lbm_create: more than 2^31 cells in total is not supported");
   }
   auto cleanup = [&](lbm_status s, const std::string& m) {
     lbm_destroy(ctx);
@@ -237,6 +238,7 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->ph.data(), ctx->pd, sizeof(ProbDev) * ctx->nprob, cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cleanup(LBM_ECUDA, std::string("lbm_create: setup: ") + cudaGetErrorString(e));
+  ctx->limf = InvLimitsF{(float)ctx->lim.x_lo, (float)ctx->lim.x_hi, (float)ctx->lim.j2_lo, (float)ctx->lim.j2_hi};
   e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cleanup(LBM_ECUDA, std::string("lbm_create: stream: ") + cudaGetErrorString(e));
   *out = ctx;

@@ -18,9 +18,10 @@ enum { STAT_FD = 0, STAT_T0 = 1, STAT_MB = 2 };
 enum { BC_PERIODIC = 0, BC_BOUNCEBACK = 1 };
 
 constexpr int kTileX = 128;  // cells of one row handled by one CTA (one per thread)
+constexpr int kTileY = 4;    // rows per CTA (each thread walks them)
 
 struct ProbDev {
-  int32_t nx, ny, pitch, bc_x, bc_y, tiles_x;
+  int32_t nx, ny, pitch, bc_x, bc_y, tiles_x;  // tiles: kTileX cells x kTileY rows
   int64_t base, tile_begin;
   double tau, omega;
   double n_ref, t_ref;               // deviation reference state (n_ref = 0: absolute storage)
@@ -141,9 +142,12 @@ __global__ void __launch_bounds__(kTileX) stream_collide_f64(const double* __res
   const int p = nprob == 1 ? 0 : find_problem(probs, nprob, tile);
   const ProbDev& P = probs[p];
   const int64_t lt = tile - P.tile_begin;
-  const int y = (int)(lt / P.tiles_x);
+  const int ty = (int)(lt / P.tiles_x);
   const int x = (int)(lt % P.tiles_x) * kTileX + threadIdx.x;
   if (x >= P.nx) return;
+  const int y1 = min(ty * kTileY + kTileY, P.ny);
+#pragma unroll 1
+  for (int y = ty * kTileY; y < y1; ++y) {
   const PullIdx q = pull_index(P, x, y);
   double f[9];
   pull9(fin, plane, q, x, f);
@@ -170,6 +174,7 @@ __global__ void __launch_bounds__(kTileX) stream_collide_f64(const double* __res
   const double w = P.omega;
 #pragma unroll
   for (int a = 0; a < 9; ++a) fout[a * plane + q.row + x] = fma(w, fe[a] - f[a], f[a]);
+  }
 }
 
 // ------------------------------------------------------------------ per-context setup
