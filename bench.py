@@ -48,6 +48,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="f32", choices=["f32", "bf16", "f64"])
     ap.add_argument("--L", type=int, default=4096)
+    ap.add_argument("--workload", default="smooth_t", choices=["smooth_t", "batched"],
+                    help="smooth_t: one 4096^2 lattice; batched: 256 uneven quasi-1D Riemann problems")
+    ap.add_argument("--autotune", action="store_true", help="autotune the tiling before timing (always on for batched)")
+    ap.add_argument("--inv", default="exact", choices=["exact", "surrogate"],
+                    help="per-cell FD inversion: exact, or the learned network (trained first, on 1e6 pairs)")
+    ap.add_argument("--train-epochs", type=int, default=32)
     ap.add_argument("--tau", type=float, default=0.8)
     ap.add_argument("--stat", default="fd", choices=["fd", "t0", "mb"],
                     help="closure: fd (per-cell inversion), t0 (theta = 0), mb (Hermite limit)")
@@ -56,7 +62,26 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(a, world):
+def workload_config(a, world, probs=None, tiling=None):
+    if a.workload == "batched":
+        cells = sum(p.cells for p in probs)
+        return {
+            "workload": f"batched_{len(probs)}_riemann",
+            "problems": len(probs),
+            "cells": cells,
+            "lengths": "log-uniform in [256, 8192]",
+            "widths": "uniform in 4..64",
+            "density_ratio": [1.05, 2.0],
+            "t_range": [0.01, 0.2],
+            "tau_range": [0.55, 1.0],
+            "boundaries": "bounce-back x, periodic y",
+            "stencil": "d2v9 K=3 generalized-polynomial LBGK, FD statistics, per-cell J2->x inversion",
+            "storage": {"f32": "FP32 deviations g = f - W_ref", "bf16": "BF16 deviations", "f64": "FP64 f"}[a.prec],
+            "launch": "all problems in one launch per step, 16-step CUDA graphs",
+            "tiling": tiling,
+            "l2": f"inputs larger than L2 ({2 * 9 * cells * BYTES_PER_ELEM[a.prec] / 1e9:.2f} GB population buffers)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        }
     return {
         "workload": f"smooth_t_{a.L}x{a.L}",
         "lattice": [a.L, a.L],
@@ -65,6 +90,8 @@ def workload_config(a, world):
                     "t0": "d2v9 K=3 generalized-polynomial LBGK, theta = 0 closure (constant J)",
                     "mb": "d2v9 K=3 LBGK, Maxwell-Boltzmann limit (J = 1)"}[a.stat],
         "storage": {"f32": "FP32 deviations g = f - W_ref", "bf16": "BF16 deviations", "f64": "FP64 f"}[a.prec],
+        "inversion": "exact (closed-form degenerate root, tail passes, Newton)" if a.inv == "exact"
+        else "learned network 2-64-64-2 + one Newton polish + residual check, exact fallback",
         "tau": a.tau,
         "t_range": [0.01, 0.2],
         "density_step": [1.0, 0.8],
@@ -260,17 +287,42 @@ def run_ours(a, world, rank, local):
 
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
-    prob = inputs.smooth_t(a.L, tau=a.tau)
-    cells = prob.cells
-    cfg = workload_config(a, world)
-    # inputs resident in HBM before the timed region
-    dev_fields = {k: torch.from_numpy(getattr(prob, k)).cuda() for k in ("n", "ux", "uy", "t")}
-    torch.cuda.synchronize()
-    lat = lbm.Lattice([prob], stat=a.stat, prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05)
+    if a.workload == "batched":
+        probs = inputs.batched()
+        prob = None
+        dev_fields = None
+        lat = lbm.Lattice(probs, stat=a.stat, prec=a.prec, stream=stream.cuda_stream, n_ref=1.2, t_ref=0.05)
+    else:
+        prob = inputs.smooth_t(a.L, tau=a.tau)
+        probs = [prob]
+        # inputs resident in HBM before the timed region
+        dev_fields = {k: torch.from_numpy(getattr(prob, k)).cuda() for k in ("n", "ux", "uy", "t")}
+        torch.cuda.synchronize()
+        lat = lbm.Lattice(probs, stat=a.stat, prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05)
+    cells = sum(p.cells for p in probs)
+    surrogate = None
+    if a.inv == "surrogate":
+        # the learned inversion: trained by the library's kernels on 1e6 pairs
+        # from the exact forward map, then loaded into a learned-inversion context
+        n_tr, t_tr = inputs.surrogate_set(1_000_000, seed=4)
+        n_va, t_va = inputs.surrogate_set(16384, seed=5)
+        net, rep = lbm.lbm_surrogate_train(inputs.surrogate_init(11), n_tr, t_tr, n_va, t_va,
+                                           epochs=a.train_epochs, batch=1024, stream=stream.cuda_stream)
+        surrogate = {"train": rep, "pairs": 1_000_000, "epochs": a.train_epochs, "batch": 1024}
+        lat.close()
+        lat = lbm.Lattice(probs, stat="fd", prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05,
+                          inv="surrogate", surrogate=net)
     with torch.cuda.stream(stream):
         lat.init(fields_on_device=dev_fields)
         lat.step(a.warmup)
     torch.cuda.synchronize()
+    tiling = None
+    if a.workload == "batched" or a.autotune:
+        with torch.cuda.stream(stream):
+            tiling = lbm.lbm_autotune(lat.ctx, 3)
+    cfg = workload_config(a, world, probs, tiling)
+    if tiling is not None and a.workload != "batched":
+        cfg["tiling"] = tiling
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -302,9 +354,17 @@ def run_ours(a, world, rank, local):
     sampler.stop()
     ms = statistics.median(times)
     ms_max = max_over_ranks(world, ms)
-    fl = lat.fields(0, diag=True)
-    nonfinite = fl["diag"]["nonfinite"] / cells
-    clamped = fl["diag"]["clamped"] / cells
+    if surrogate is not None:
+        st = lbm.lbm_surrogate_stats(lat.ctx)
+        surrogate["fallback_frac"] = st["fallbacks"] / max(st["evaluations"], 1)
+        cfg["inversion"] = surrogate
+    nonfinite = clamped = 0
+    for i in range(len(probs)):
+        d = lbm.lbm_moments(lat.ctx, i, diag=True)
+        nonfinite += d["nonfinite"]
+        clamped += d["clamped"]
+    nonfinite /= cells
+    clamped /= cells
     lat.close()
 
     value = world * cells * a.steps / (ms_max / 1e3) / 1e6
@@ -314,6 +374,8 @@ def run_ours(a, world, rank, local):
     peak, peak_kind = peaks()
     kname = {"f32": "stream_collide_dev<float,%s>", "bf16": "stream_collide_dev<bf16,%s>",
              "f64": "stream_collide_f64<%s>"}[a.prec] % a.stat.upper()
+    if a.inv == "surrogate":
+        kname = {"f32": "stream_collide_surr<float>", "bf16": "stream_collide_surr<bf16>"}[a.prec]
     traffic = profiled_traffic(kname, cells)
     out = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
@@ -329,7 +391,7 @@ def run_ours(a, world, rank, local):
                           "note": "each window: fresh init, warm-up steps, then the timed steps"},
         "state_after_timed_steps": {"nonfinite_frac": nonfinite, "clamped_frac": clamped},
     }
-    if not a.no_extras and rank == 0:
+    if not a.no_extras and rank == 0 and a.workload == "smooth_t":
         out.update(extras(a, prob, dev_fields, lbm, torch, stream, value))
     del dev_fields
     if rank == 0:

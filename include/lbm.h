@@ -128,6 +128,30 @@ lbm_status lbm_init_riemann(lbm_ctx* ctx, int32_t problem, const lbm_riemann_des
  * Asynchronous.  Errors: LBM_EINVAL (nsteps < 0), LBM_ECUDA. */
 lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps);
 
+/* Tiling of the step launch.  A tile is 128 consecutive cells of
+ * rows_per_tile consecutive rows of one problem (1, 2, 4 or 8 rows); every
+ * problem of the context is cut into tiles and all tiles advance in one
+ * launch per step.  ctas = 0 launches one CTA per tile; ctas > 0 launches that
+ * many CTAs (a persistent grid) that walk the tiles in turn.  The default is
+ * 4 rows, one CTA per tile. */
+typedef struct {
+  int32_t rows_per_tile;
+  int32_t ctas;
+  double ms_per_step; /* lbm_autotune: measured time of the chosen tiling */
+} lbm_tiling;
+
+/* Set the tiling (drops captured graphs).  Synchronises the context's stream.
+ * Errors: LBM_EINVAL (rows not in {1, 2, 4, 8}, ctas < 0), LBM_ECUDA. */
+lbm_status lbm_set_tiling(lbm_ctx* ctx, int32_t rows_per_tile, int32_t ctas);
+lbm_status lbm_get_tiling(const lbm_ctx* ctx, lbm_tiling* out);
+
+/* Time rows {1, 2, 4, 8} x ctas {one per tile, 4, 8 and 16 per SM} on the
+ * context's own problems (steps_per_candidate timed steps each, after one
+ * untimed step) and keep the fastest.  Each trial reads the current
+ * populations and writes only the other buffer, so the state is unchanged.
+ * Synchronises the stream; chosen may be NULL.  Errors: LBM_EINVAL, LBM_ECUDA. */
+lbm_status lbm_autotune(lbm_ctx* ctx, int32_t steps_per_candidate, lbm_tiling* chosen);
+
 /* Per-run diagnostics of lbm_moments: totals over the problem's cells (FP64,
  * summed in a fixed order, so identical states give identical sums) and
  * counts of cells whose inversion was clamped to t in [1e-3, 10] or whose
@@ -166,6 +190,73 @@ const char* lbm_last_error(const lbm_ctx* ctx);
 /* Number of kernel launches issued by the library on this context since it
  * was created (graph replays count each captured kernel). */
 int64_t lbm_launch_count(const lbm_ctx* ctx);
+
+/* ---------------------------------------------------------------- learned inversion
+ * A network stands in for the per-cell inversion J_2 -> x (x = mu/T) of the
+ * FD moment ratio (the FD form of I_2N, Sect. "Generalized polynomials in D
+ * dimensions"); the paper has no network, the model is this library's:
+ *   inputs    (n, e), e = D n J_2/3 (D = 2) the internal energy in lattice
+ *             units; fixed embedding n_hat = (n - 1.25)/0.75 and
+ *             l_hat = (ln delta + 5.3)/3.7, delta = 3/2 - 3 e/(2 n)
+ *   layers    h1 = silu(W1 x + b1), h2 = silu(W2 h1 + b2), y = W3 h2 + b3,
+ *             64 hidden units each, silu(z) = z/(1 + e^{-z})
+ *   outputs   ln T = 0.5 y_0 - 5.09, mu = 0.12 y_1 + 0.1985 (T, mu in the
+ *             paper's units)
+ *   parameters, FP32, in this order: W1 [64][2], b1 [64], W2 [64][64], b2 [64],
+ *             W3 [2][64], b3 [2] (row-major [out][in]): 4482 values.
+ * A context created with inv = LBM_INV_SURROGATE (FD statistics, FP32 or BF16
+ * storage) evaluates the network per cell inside the step, polishes x = mu/T
+ * by one Newton step on J_2(x) and falls back to the exact inversion when that
+ * step is not below 5e-4 x. */
+#define LBM_SURROGATE_NPARAM 4482
+
+typedef struct {
+  int32_t epochs;  /* passes over the training set (>= 1) */
+  int32_t batch;   /* samples per step, a multiple of 128 */
+  float lr;        /* Adam learning rate at the start (cosine decay) */
+  float lr_final;  /* learning rate at the end (<= 0: lr/100) */
+} lbm_train_cfg;
+
+typedef struct {
+  int64_t iterations;
+  double loss_first, loss_last;  /* mean squared error of the normalised outputs, first and last batch */
+  double val_rmse_lnT, val_rmse_mu, val_max_rel_x; /* on the validation set (-1 if none) */
+  double seconds;
+} lbm_train_report;
+
+/* Features (n_hat, l_hat) and normalised targets of the exact forward map of
+ * the method for states (n, t = T/T_F): x = x(t), J_2 = J_2(x), e = 2 n J_2/3,
+ * T = n t/(2 pi), mu = T x.  feat, targ: count x 2 floats.  on_device: all
+ * four arrays are device memory.  Synchronises.  Errors: LBM_EINVAL, LBM_ECUDA. */
+lbm_status lbm_surrogate_targets(const double* n, const double* t, int64_t count, int32_t on_device, float* feat,
+                                 float* targ, void* cuda_stream);
+
+/* Mean squared error of the normalised outputs and its gradient with respect
+ * to the 4482 parameters, over count samples (host arrays; count <= 2^24).
+ * Synchronises.  Errors: LBM_EINVAL, LBM_ECUDA. */
+lbm_status lbm_surrogate_loss_grad(const float* params, const float* feat, const float* targ, int64_t count,
+                                   float* grad, double* loss, void* cuda_stream);
+
+/* Train the network on states (n, t) (count >= 128; optional validation set)
+ * with Adam; params (host, 4482 floats) holds the initial values on entry and
+ * the trained ones on return.  Deterministic for fixed inputs.  on_device
+ * refers to n, t, n_val, t_val.  Synchronises.  Errors: LBM_EINVAL, LBM_ECUDA. */
+lbm_status lbm_surrogate_train(const double* n, const double* t, int64_t count, const double* n_val,
+                               const double* t_val, int64_t count_val, int32_t on_device, const lbm_train_cfg* cfg,
+                               float* params, lbm_train_report* rep, void* cuda_stream);
+
+/* (T, mu) predicted by the network for count cells (n, e). */
+lbm_status lbm_surrogate_eval(const float* params, const double* n, const double* e, int64_t count, double* T,
+                              double* mu, int32_t on_device, void* cuda_stream);
+
+/* Give a learned-inversion context its network (host array of 4482 floats,
+ * copied; drops captured graphs).  Errors: LBM_EINVAL (not a learned-inversion
+ * context, NULL, non-finite values), LBM_ENOMEM. */
+lbm_status lbm_surrogate_load(lbm_ctx* ctx, const float* params);
+
+/* Cells that went through the network, and those that fell back to the exact
+ * inversion, since the context was created.  Synchronises. */
+lbm_status lbm_surrogate_stats(lbm_ctx* ctx, int64_t* fallbacks, int64_t* evaluations);
 
 /* lbm_conservation_sums_static - the paper has no counterpart to this call;
  * it exists for callers that cannot allocate device memory.

@@ -12,15 +12,77 @@
 #include <string>
 #include <vector>
 
+#include "launch.h"
 #include "lbm.h"
 #include "lbm_kernels.cuh"
-#include "lbm_dev32.cuh"
+#include "surrogate.cuh"
 
 using namespace lbm;
 
 namespace {
 
 constexpr int kGraphChunk = 16;  // steps per captured graph (even: buffers return)
+
+// ------------------------------------------------------------------ per-context setup
+
+static __global__ void setup_kernel(InvLimits* out) {
+  InvLimits L;
+  L.x_lo = x_of_t(kTMax);
+  L.x_hi = x_of_t(kTMin);
+  L.j2_lo = j2_of(fd_eval(L.x_lo));
+  L.j2_hi = j2_of(fd_eval(L.x_hi));
+  *out = L;
+}
+
+// Deviation reference of each problem: J_2,ref from t_ref (or the closure's
+// constant), W^ref = w_a(J_2,ref) n_ref and n_ref (3/2 - J_2,ref).
+static __global__ void ref_kernel(ProbDev* probs, int nprob, int stat) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nprob) return;
+  ProbDev& P = probs[p];
+  double J2, J4;
+  if (stat == STAT_FD) {
+    if (P.n_ref > 0.0) closure_from_t<STAT_FD>(P.t_ref, J2, J4); else J2 = 1.5;
+  } else if (stat == STAT_T0) {
+    J2 = FixedJ<STAT_T0>::j2;
+  } else {
+    J2 = FixedJ<STAT_MB>::j2;
+  }
+  const double n = P.n_ref;
+  const double w0 = n * (1.0 - 5.0 * J2 / 9.0), ws = n * J2 / 9.0, wl = n * J2 / 36.0;
+  P.j2_ref = J2;
+  P.ndelta_ref = n * (1.5 - J2);
+  P.wref[0] = w0;
+  for (int a = 1; a <= 4; ++a) P.wref[a] = ws;
+  for (int a = 5; a <= 8; ++a) P.wref[a] = wl;
+  P.f.omega = (float)P.omega;
+  P.f.n_ref = (float)n;
+  P.f.ndelta_ref = (float)P.ndelta_ref;
+  P.f.wref[0] = (float)w0;
+  P.f.wref[1] = (float)ws;
+  P.f.wref[2] = (float)wl;
+}
+
+
+// One block sums the per-block partials in a fixed order.
+static __global__ void __launch_bounds__(256) reduce_partials_kernel(const double* __restrict__ partials, int64_t nblocks,
+                                                              double* __restrict__ out) {
+  __shared__ double sh[256];
+  for (int k = 0; k < kNPartial; ++k) {
+    double s = 0.0;
+    for (int64_t b = threadIdx.x; b < nblocks; b += 256) s += partials[b * kNPartial + k];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = sh[0];
+    __syncthreads();
+  }
+}
+
+
 
 std::mutex g_err_mu;
 std::string g_create_err;
@@ -35,6 +97,8 @@ struct lbm_ctx {
   std::vector<ProbDev> ph;  // host copy of the device table
   ProbDev* pd = nullptr;
   int64_t plane = 0, ntiles = 0;
+  int rows = kTileYDefault;  // rows per tile
+  int ctas = 0;              // 0: one CTA per tile; else a persistent grid of this many CTAs
   void* buf[2] = {nullptr, nullptr};
   int cur = 0;
   cudaStream_t stream = nullptr;
@@ -50,6 +114,8 @@ struct lbm_ctx {
   int64_t tmp_cap = 0;
   int64_t launches = 0;
   std::string err;
+  MlpParams* surr = nullptr;               // host copy of the network (learned inversion)
+  unsigned long long* surr_count = nullptr;  // device: fallbacks, evaluations
 };
 
 namespace {
@@ -78,29 +144,37 @@ lbm_status fail(lbm_ctx* ctx, lbm_status s, const std::string& m) {
 
 unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-template <int STAT>
-void launch_step_stat(lbm_ctx* c, const void* in, void* out, cudaStream_t s) {
-  const unsigned g = (unsigned)c->ntiles;
+void launch_step(lbm_ctx* c, const void* in, void* out, cudaStream_t s) {
+  StepArgs a{in, out, c->pd, c->nprob, (int)c->ntiles, c->plane, c->lim, c->limf};
+  const unsigned grid = c->ctas > 0 ? (unsigned)std::min<int64_t>(c->ctas, c->ntiles) : (unsigned)c->ntiles;
+  if (c->inv == LBM_INV_SURROGATE) {
+    if (c->prec == LBM_F32_DEV)
+      launch_step_surr_f32(c->rows, grid, s, a, c->surr_count, *c->surr);
+    else
+      launch_step_surr_bf16(c->rows, grid, s, a, c->surr_count, *c->surr);
+    return;
+  }
   switch (c->prec) {
-    case LBM_F64:
-      stream_collide_f64<STAT><<<g, kTileX, 0, s>>>((const double*)in, (double*)out, c->pd, c->nprob, c->plane, c->lim);
-      break;
-    case LBM_F32_DEV:
-      stream_collide_dev<float, STAT><<<g, kTileX, 0, s>>>((const float*)in, (float*)out, c->pd, c->nprob, c->plane,
-                                                             c->lim, c->limf);
-      break;
-    default:
-      stream_collide_dev<__nv_bfloat16, STAT><<<g, kTileX, 0, s>>>((const __nv_bfloat16*)in, (__nv_bfloat16*)out,
-                                                                     c->pd, c->nprob, c->plane, c->lim, c->limf);
-      break;
+    case LBM_F64: launch_step_f64(c->stat, c->rows, grid, s, a); break;
+    case LBM_F32_DEV: launch_step_f32(c->stat, c->rows, grid, s, a); break;
+    default: launch_step_bf16(c->stat, c->rows, grid, s, a); break;
   }
 }
 
-void launch_step(lbm_ctx* c, const void* in, void* out, cudaStream_t s) {
-  switch (c->stat) {
-    case LBM_STAT_FD: launch_step_stat<STAT_FD>(c, in, out, s); break;
-    case LBM_STAT_FD_T0: launch_step_stat<STAT_T0>(c, in, out, s); break;
-    default: launch_step_stat<STAT_MB>(c, in, out, s); break;
+// Tile table for `rows` rows per tile: first tile of every problem, total.
+int64_t layout_tiles(std::vector<ProbDev>& ph, int rows) {
+  int64_t tiles = 0;
+  for (auto& d : ph) {
+    d.tile_begin = tiles;
+    tiles += (int64_t)d.tiles_x * ((d.ny + rows - 1) / rows);
+  }
+  return tiles;
+}
+
+void drop_graphs(lbm_ctx* c) {
+  for (int b = 0; b < 2; ++b) {
+    if (c->graph[b]) cudaGraphExecDestroy(c->graph[b]);
+    c->graph[b] = nullptr;
   }
 }
 
@@ -164,8 +238,9 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
   if (p->stat < 0 || p->stat > 2) return fail(nullptr, LBM_EINVAL, "lbm_create: bad stat");
   if (p->prec < 0 || p->prec > 2) return fail(nullptr, LBM_EINVAL, "lbm_create: bad prec");
   if (p->inv != LBM_INV_EXACT && p->inv != LBM_INV_SURROGATE) return fail(nullptr, LBM_EINVAL, "lbm_create: bad inv");
-  if (p->inv == LBM_INV_SURROGATE)
-    return fail(nullptr, LBM_EUNSUPPORTED, "lbm_create: the surrogate inversion is not built into this library");
+  if (p->inv == LBM_INV_SURROGATE && (p->prec == LBM_F64 || p->stat != LBM_STAT_FD))
+    return fail(nullptr, LBM_EUNSUPPORTED,
+                "lbm_create: the learned inversion needs LBM_STAT_FD with FP32 or BF16 deviation storage");
   if (p->nproblems < 1 || !p->problems) return fail(nullptr, LBM_EINVAL, "lbm_create: no problems");
   for (int i = 0; i < p->nproblems; ++i) {
     const lbm_problem& q = p->problems[i];
@@ -188,7 +263,7 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
   ctx->nprob = p->nproblems;
   ctx->probs.assign(p->problems, p->problems + p->nproblems);
   ctx->stream = (cudaStream_t)cuda_stream;
-  int64_t base = 0, tiles = 0;
+  int64_t base = 0;
   for (int i = 0; i < ctx->nprob; ++i) {
     const lbm_problem& q = ctx->probs[i];
     ProbDev d{};
@@ -199,15 +274,14 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
     d.bc_y = q.bc_y;
     d.tiles_x = (q.nx + kTileX - 1) / kTileX;
     d.base = base;
-    d.tile_begin = tiles;
     d.tau = q.tau;
     d.omega = 1.0 / q.tau;
     d.n_ref = p->prec == LBM_F64 ? 0.0 : q.n_ref;
     d.t_ref = p->prec == LBM_F64 ? 0.0 : q.t_ref;
     base += (int64_t)d.pitch * q.ny;
-    tiles += (int64_t)d.tiles_x * ((q.ny + kTileY - 1) / kTileY);
     ctx->ph.push_back(d);
   }
+  const int64_t tiles = layout_tiles(ctx->ph, ctx->rows);
   ctx->plane = (base + 31) / 32 * 32;
   ctx->ntiles = tiles;
   if (tiles > 0x7fffffffLL || ctx->plane > 0x7fffffffLL) {
@@ -228,6 +302,10 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
   cudaError_t e = cudaMalloc(&ctx->pd, sizeof(ProbDev) * ctx->nprob);
   if (e == cudaSuccess) e = cudaMalloc(&ctx->lim_d, sizeof(InvLimits));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->diag_d, sizeof(double) * kNPartial);
+  if (e == cudaSuccess && p->inv == LBM_INV_SURROGATE) {
+    e = cudaMalloc(&ctx->surr_count, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->surr_count, 0, 2 * sizeof(unsigned long long), ctx->stream);
+  }
   if (e != cudaSuccess) return cleanup(LBM_ENOMEM, std::string("lbm_create: tables: ") + cudaGetErrorString(e));
   e = cudaMemcpyAsync(ctx->pd, ctx->ph.data(), sizeof(ProbDev) * ctx->nprob, cudaMemcpyHostToDevice, ctx->stream);
   if (e != cudaSuccess) return cleanup(LBM_ECUDA, std::string("lbm_create: upload: ") + cudaGetErrorString(e));
@@ -303,6 +381,8 @@ lbm_status lbm_init_riemann(lbm_ctx* ctx, int32_t problem, const lbm_riemann_des
 lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps) {
   if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_step: NULL context");
   if (nsteps < 0) return fail(ctx, LBM_EINVAL, "lbm_step: nsteps < 0");
+  if (ctx->inv == LBM_INV_SURROGATE && !ctx->surr)
+    return fail(ctx, LBM_EINVAL, "lbm_step: load the network with lbm_surrogate_load first");
   while (nsteps >= kGraphChunk) {
     cudaGraphExec_t& ge = ctx->graph[ctx->cur];
     if (!ge) {
@@ -335,6 +415,121 @@ lbm_status lbm_step(lbm_ctx* ctx, int32_t nsteps) {
     CKL();
     ctx->cur ^= 1;
     ctx->launches += 1;
+  }
+  return LBM_OK;
+}
+
+namespace {
+
+lbm_status apply_tiling(lbm_ctx* ctx, int rows, int ctas) {
+  std::vector<ProbDev> ph = ctx->ph;
+  const int64_t tiles = layout_tiles(ph, rows);
+  if (tiles > 0x7fffffffLL) return fail(ctx, LBM_EINVAL, "lbm_set_tiling: too many tiles");
+  CK(cudaMemcpyAsync(ctx->pd, ph.data(), sizeof(ProbDev) * ctx->nprob, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));  // the host copy `ph` must outlive the transfer
+  ctx->ph = ph;
+  ctx->ntiles = tiles;
+  ctx->rows = rows;
+  ctx->ctas = ctas;
+  drop_graphs(ctx);
+  return LBM_OK;
+}
+
+}  // namespace
+
+lbm_status lbm_set_tiling(lbm_ctx* ctx, int32_t rows_per_tile, int32_t ctas) {
+  if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_set_tiling: NULL context");
+  if (!valid_rows(rows_per_tile)) return fail(ctx, LBM_EINVAL, "lbm_set_tiling: rows_per_tile must be 1, 2, 4 or 8");
+  if (ctas < 0) return fail(ctx, LBM_EINVAL, "lbm_set_tiling: ctas must be >= 0");
+  return apply_tiling(ctx, rows_per_tile, ctas);
+}
+
+lbm_status lbm_get_tiling(const lbm_ctx* ctx, lbm_tiling* out) {
+  if (!ctx || !out) return LBM_EINVAL;
+  out->rows_per_tile = ctx->rows;
+  out->ctas = ctx->ctas;
+  out->ms_per_step = 0.0;
+  return LBM_OK;
+}
+
+lbm_status lbm_surrogate_load(lbm_ctx* ctx, const float* params) {
+  if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_surrogate_load: NULL context");
+  if (!params) return fail(ctx, LBM_EINVAL, "lbm_surrogate_load: NULL parameters");
+  if (ctx->inv != LBM_INV_SURROGATE)
+    return fail(ctx, LBM_EINVAL, "lbm_surrogate_load: the context was created with the exact inversion");
+  for (int i = 0; i < kNParam; ++i)
+    if (!std::isfinite(params[i])) return fail(ctx, LBM_EINVAL, "lbm_surrogate_load: non-finite parameter");
+  if (!ctx->surr) ctx->surr = new (std::nothrow) MlpParams();
+  if (!ctx->surr) return fail(ctx, LBM_ENOMEM, "lbm_surrogate_load: host allocation failed");
+  std::memcpy(ctx->surr->p, params, sizeof(float) * kNParam);
+  drop_graphs(ctx);
+  return LBM_OK;
+}
+
+lbm_status lbm_surrogate_stats(lbm_ctx* ctx, int64_t* fallbacks, int64_t* evaluations) {
+  if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_surrogate_stats: NULL context");
+  if (!ctx->surr_count) return fail(ctx, LBM_EINVAL, "lbm_surrogate_stats: not a learned-inversion context");
+  unsigned long long h[2] = {0, 0};
+  CK(cudaMemcpyAsync(h, ctx->surr_count, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (fallbacks) *fallbacks = (int64_t)h[0];
+  if (evaluations) *evaluations = (int64_t)h[1];
+  return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_ctx* ctx, int32_t steps_per_candidate, lbm_tiling* chosen) {
+  if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_autotune: NULL context");
+  if (ctx->inv == LBM_INV_SURROGATE && !ctx->surr)
+    return fail(ctx, LBM_EINVAL, "lbm_autotune: load the network with lbm_surrogate_load first");
+  if (steps_per_candidate < 1) return fail(ctx, LBM_EINVAL, "lbm_autotune: steps_per_candidate must be >= 1");
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int rows_c[4] = {1, 2, 4, 8};
+  const int ctas_c[4] = {0, 4 * sms, 8 * sms, 16 * sms};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best = 1e300;
+  int best_r = ctx->rows, best_c = ctx->ctas;
+  lbm_status st = LBM_OK;
+  // Every candidate reads the current buffer and writes the other one only:
+  // the state the caller sees does not change.
+  for (int ri = 0; ri < 4 && st == LBM_OK; ++ri) {
+    for (int ci = 0; ci < 4 && st == LBM_OK; ++ci) {
+      st = apply_tiling(ctx, rows_c[ri], ctas_c[ci]);
+      if (st != LBM_OK) break;
+      launch_step(ctx, ctx->buf[ctx->cur], ctx->buf[ctx->cur ^ 1], ctx->stream);
+      cudaEventRecord(e0, ctx->stream);
+      for (int k = 0; k < steps_per_candidate; ++k)
+        launch_step(ctx, ctx->buf[ctx->cur], ctx->buf[ctx->cur ^ 1], ctx->stream);
+      cudaEventRecord(e1, ctx->stream);
+      ctx->launches += steps_per_candidate + 1;
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        st = fail(ctx, LBM_ECUDA, std::string("lbm_autotune: ") + cudaGetErrorString(e));
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double per = (double)ms / steps_per_candidate;
+      if (per < best) {
+        best = per;
+        best_r = rows_c[ri];
+        best_c = ctas_c[ci];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != LBM_OK) return st;
+  st = apply_tiling(ctx, best_r, best_c);
+  if (st != LBM_OK) return st;
+  if (chosen) {
+    chosen->rows_per_tile = best_r;
+    chosen->ctas = best_c;
+    chosen->ms_per_step = best;
   }
   return LBM_OK;
 }
@@ -448,8 +643,8 @@ lbm_status lbm_set_populations(lbm_ctx* ctx, int32_t problem, const double* f, i
 lbm_status lbm_destroy(lbm_ctx* ctx) {
   if (!ctx) return LBM_OK;
   cudaStreamSynchronize(ctx->stream);
+  drop_graphs(ctx);
   for (int b = 0; b < 2; ++b) {
-    if (ctx->graph[b]) cudaGraphExecDestroy(ctx->graph[b]);
     if (ctx->buf[b]) cudaFree(ctx->buf[b]);
   }
   if (ctx->pd) cudaFree(ctx->pd);
@@ -458,6 +653,8 @@ lbm_status lbm_destroy(lbm_ctx* ctx) {
   if (ctx->partials) cudaFree(ctx->partials);
   if (ctx->tmp) cudaFree(ctx->tmp);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
+  if (ctx->surr_count) cudaFree(ctx->surr_count);
+  delete ctx->surr;
   delete ctx;
   return LBM_OK;
 }

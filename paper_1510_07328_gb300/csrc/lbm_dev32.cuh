@@ -16,16 +16,14 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include "launch.h"
 #include "lbm_kernels.cuh"
+#include "surrogate.cuh"
 
 namespace lbm {
 
 constexpr float kPi2f = 9.8696044010893586f;
 constexpr float kXDegF = 17.0f;  // e^-17 = 4e-8: S_n tails below FP32 resolution
-
-struct InvLimitsF {
-  float x_lo, x_hi, j2_lo, j2_hi;
-};
 
 template <class T>
 struct Dev;
@@ -276,6 +274,45 @@ __device__ __forceinline__ float j4_from_delta_f(float delta, const InvLimitsF& 
   return J4;
 }
 
+// J_4 through the learned inversion: the network gives (T, mu) from (n, e),
+// e = 2 n J_2/3, hence x_0 = mu/T; one Newton step on J_2(x) = J_2 polishes
+// it to x_1; the residual check evaluates f_0..f_4 at x_1 and accepts when the
+// remaining Newton correction dx is below 5e-4 x_1 (the acceptance of the
+// exact iteration), returning J_4(x_1) + J_4'(x_1) dx.  Otherwise *fallback is
+// set and the exact inversion runs.
+__device__ __forceinline__ float j4_surrogate_f(float n, float delta, const InvLimitsF& L, const MlpParams& W,
+                                                int* fallback) {
+  const float J2 = 1.5f - delta;
+  if (!(J2 == J2) || !(J2 < L.j2_hi) || J2 <= L.j2_lo) {  // non-finite or clamped: the exact path handles it
+    float xx;
+    return j4_from_delta_f(delta, L, &xx);
+  }
+  float y0, y1, T, mu;
+  mlp_forward_f(W, n, delta, y0, y1);  // e = 2 n J_2/3 enters as delta = 3/2 - J_2
+  mlp_outputs_to_state(y0, y1, T, mu);
+  float x = fminf(fmaxf(mu * rcp_a(T), L.x_lo), L.x_hi);
+#pragma unroll 1
+  for (int it = 0; it < 2; ++it) {
+    const FD5f f = x >= 4.0f ? fd_eval_deg_f(x) : fd_eval_f(x);
+    const float i1 = rcp_a(f.f1), i2 = rcp_a(f.f2), i3 = rcp_a(f.f3), i4 = rcp_a(f.f4);
+    const float j = f.f2 * f.f2 * i1 * i3;
+    const float dj = j * (2.0f * f.f1 * i2 - f.f0 * i1 - f.f2 * i3);
+    const float dx = (J2 - j) * rcp_a(dj);
+    if (it == 1) {
+      if (fabsf(dx) < 5e-4f * x) {
+        const float J4 = f.f3 * f.f3 * i2 * i4;
+        const float dJ4 = J4 * (2.0f * f.f2 * i3 - f.f1 * i2 - f.f3 * i4);
+        return J4 + dJ4 * dx;
+      }
+      break;
+    }
+    x = fminf(fmaxf(x + dx, L.x_lo), L.x_hi);
+  }
+  *fallback = 1;
+  float xx;
+  return j4_from_delta_f(delta, L, &xx);
+}
+
 // 32-bit in-plane pull offsets (every plane holds fewer than 2^31 cells);
 // -1 marks an off-lattice source.
 struct PullIdx32 {
@@ -312,9 +349,10 @@ __device__ __forceinline__ void pull9_32(const T* __restrict__ fin, int64_t plan
 }
 
 // Collision of one cell from its pulled deviations g[9]; stores at `off`.
-template <class T, int STAT>
+template <class T, int STAT, bool SURR = false>
 __device__ __forceinline__ void collide_store_dev(const ProbDev& P, const float g[9], T* __restrict__ fout,
-                                                  int64_t plane, int off, const InvLimitsF& L) {
+                                                  int64_t plane, int off, const InvLimitsF& L,
+                                                  const MlpParams* W = nullptr, int* fallback = nullptr) {
   const float nref = P.f.n_ref, ndref = P.f.ndelta_ref;
   const float dn = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
   const float jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
@@ -329,8 +367,12 @@ __device__ __forceinline__ void collide_store_dev(const ProbDev& P, const float 
   if (STAT == STAT_FD) {
     const float delta = (ndref + 1.5f * X) * in;  // 3/2 - J_2
     J2 = 1.5f - delta;
-    float xx;
-    J4 = j4_from_delta_f(delta, L, &xx);
+    if (SURR) {
+      J4 = j4_surrogate_f(n, delta, L, *W, fallback);
+    } else {
+      float xx;
+      J4 = j4_from_delta_f(delta, L, &xx);
+    }
   } else {
     J2 = (float)FixedJ<STAT>::j2;
     J4 = (float)FixedJ<STAT>::j4;
@@ -402,37 +444,83 @@ __device__ __forceinline__ int gather_dev(const T* __restrict__ fin, int64_t pla
   return q.row + x;
 }
 
-// One CTA: kTileX consecutive cells of kTileY consecutive rows of one problem.
+// One tile: kTileX consecutive cells of TY consecutive rows of one problem.
+// PERSIST = false: one tile per CTA (grid = number of tiles).  PERSIST = true:
+// a smaller grid whose CTAs walk tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // Tiles whose cells and neighbours are all inside the lattice (no wall, no
 // wrap) take the branch-free interior gather; edge tiles take the general one.
 // The next row's nine loads are issued before the current row's collision so
 // that each thread keeps two rows of loads in flight.
-template <class T, int STAT>
+template <class T, int STAT, int TY, bool PERSIST>
 __global__ void __launch_bounds__(kTileX, 10) stream_collide_dev(const T* __restrict__ fin, T* __restrict__ fout,
-                                                             const ProbDev* __restrict__ probs, int nprob,
-                                                             int64_t plane, InvLimits Ld, InvLimitsF L) {
-  const int tile = (int)blockIdx.x;
-  const int p = nprob == 1 ? 0 : find_problem(probs, nprob, tile);
-  const ProbDev& P = probs[p];
-  const int lt = tile - (int)P.tile_begin;
-  const int ty = lt / P.tiles_x;
-  const int x0 = (lt - ty * P.tiles_x) * kTileX;
-  const int x = x0 + (int)threadIdx.x;
-  if (x >= P.nx) return;
-  const int y0 = ty * kTileY;
-  const int y1 = min(y0 + kTileY, P.ny);
-  const bool xin = x0 >= 1 && x0 + kTileX <= P.nx - 1;
-  float gn[9];
-  int offn = gather_dev(fin, plane, P, x, y0, xin, gn);
+                                                                 const ProbDev* __restrict__ probs, int nprob,
+                                                                 int ntiles, int64_t plane, InvLimitsF L) {
+  int tile = (int)blockIdx.x;
 #pragma unroll 1
-  for (int y = y0; y < y1; ++y) {
-    float g[9];
+  do {
+    const int p = nprob == 1 ? 0 : find_problem(probs, nprob, tile);
+    const ProbDev& P = probs[p];
+    const int lt = tile - (int)P.tile_begin;
+    const int ty = lt / P.tiles_x;
+    const int x0 = (lt - ty * P.tiles_x) * kTileX;
+    const int x = x0 + (int)threadIdx.x;
+    if (x < P.nx) {
+      const int y0 = ty * TY;
+      const int y1 = min(y0 + TY, P.ny);
+      const bool xin = x0 >= 1 && x0 + kTileX <= P.nx - 1;
+      float gn[9];
+      int offn = gather_dev(fin, plane, P, x, y0, xin, gn);
+#pragma unroll 1
+      for (int y = y0; y < y1; ++y) {
+        float g[9];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) g[a] = gn[a];
-    const int off = offn;
-    if (y + 1 < y1) offn = gather_dev(fin, plane, P, x, y + 1, xin, gn);
-    collide_store_dev<T, STAT>(P, g, fout, plane, off, L);
-  }
+        for (int a = 0; a < 9; ++a) g[a] = gn[a];
+        const int off = offn;
+        if (y + 1 < y1) offn = gather_dev(fin, plane, P, x, y + 1, xin, gn);
+        collide_store_dev<T, STAT>(P, g, fout, plane, off, L);
+      }
+    }
+  } while (PERSIST && (tile += (int)gridDim.x) < ntiles);
+}
+
+// The FD step with the learned inversion (see j4_surrogate_f).  counters[0]
+// accumulates cells that fell back to the exact inversion, counters[1] cells
+// that went through the network (one atomic per warp and row).
+template <class T, int TY, bool PERSIST>
+__global__ void __launch_bounds__(kTileX) stream_collide_surr(const T* __restrict__ fin, T* __restrict__ fout,
+                                                              const ProbDev* __restrict__ probs, int nprob, int ntiles,
+                                                              int64_t plane, InvLimitsF L,
+                                                              unsigned long long* __restrict__ counters,
+                                                              const MlpParams W) {
+  int tile = (int)blockIdx.x;
+#pragma unroll 1
+  do {
+    const int p = nprob == 1 ? 0 : find_problem(probs, nprob, tile);
+    const ProbDev& P = probs[p];
+    const int lt = tile - (int)P.tile_begin;
+    const int ty = lt / P.tiles_x;
+    const int x0 = (lt - ty * P.tiles_x) * kTileX;
+    const int x = x0 + (int)threadIdx.x;
+    const int y0 = ty * TY;
+    const int y1 = min(y0 + TY, P.ny);
+    const bool xin = x0 >= 1 && x0 + kTileX <= P.nx - 1;
+#pragma unroll 1
+    for (int y = y0; y < y1; ++y) {
+      int fb = 0;
+      const bool active = x < P.nx;
+      if (active) {
+        float g[9];
+        const int off = gather_dev(fin, plane, P, x, y, xin, g);
+        collide_store_dev<T, STAT_FD, true>(P, g, fout, plane, off, L, &W, &fb);
+      }
+      const unsigned nfb = __ballot_sync(0xffffffffu, fb != 0);
+      const unsigned nact = __ballot_sync(0xffffffffu, active);
+      if ((threadIdx.x & 31) == 0 && nact) {
+        atomicAdd(&counters[0], (unsigned long long)__popc(nfb));
+        atomicAdd(&counters[1], (unsigned long long)__popc(nact));
+      }
+    }
+  } while (PERSIST && (tile += (int)gridDim.x) < ntiles);
 }
 
 }  // namespace lbm

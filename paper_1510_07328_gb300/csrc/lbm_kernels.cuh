@@ -17,11 +17,11 @@ namespace lbm {
 enum { STAT_FD = 0, STAT_T0 = 1, STAT_MB = 2 };
 enum { BC_PERIODIC = 0, BC_BOUNCEBACK = 1 };
 
-constexpr int kTileX = 128;  // cells of one row handled by one CTA (one per thread)
-constexpr int kTileY = 4;    // rows per CTA (each thread walks them)
+constexpr int kTileX = 128;      // cells of one row handled by one CTA (one per thread)
+constexpr int kTileYDefault = 4; // rows per tile (each thread walks them); tunable: 1, 2, 4, 8
 
 struct ProbDev {
-  int32_t nx, ny, pitch, bc_x, bc_y, tiles_x;  // tiles: kTileX cells x kTileY rows
+  int32_t nx, ny, pitch, bc_x, bc_y, tiles_x;  // tiles: kTileX cells x (rows per tile) rows
   int64_t base, tile_begin;
   double tau, omega;
   double n_ref, t_ref;               // deviation reference state (n_ref = 0: absolute storage)
@@ -134,87 +134,49 @@ __device__ __forceinline__ void pull9(const T* __restrict__ fin, int64_t plane, 
 
 // ------------------------------------------------------------------ FP64 step
 
-template <int STAT>
+template <int STAT, int TY, bool PERSIST>
 __global__ void __launch_bounds__(kTileX) stream_collide_f64(const double* __restrict__ fin, double* __restrict__ fout,
-                                                             const ProbDev* __restrict__ probs, int nprob,
+                                                             const ProbDev* __restrict__ probs, int nprob, int ntiles,
                                                              int64_t plane, InvLimits L) {
-  const int64_t tile = blockIdx.x;
-  const int p = nprob == 1 ? 0 : find_problem(probs, nprob, tile);
-  const ProbDev& P = probs[p];
-  const int64_t lt = tile - P.tile_begin;
-  const int ty = (int)(lt / P.tiles_x);
-  const int x = (int)(lt % P.tiles_x) * kTileX + threadIdx.x;
-  if (x >= P.nx) return;
-  const int y1 = min(ty * kTileY + kTileY, P.ny);
+  int tile = (int)blockIdx.x;
 #pragma unroll 1
-  for (int y = ty * kTileY; y < y1; ++y) {
-  const PullIdx q = pull_index(P, x, y);
-  double f[9];
-  pull9(fin, plane, q, x, f);
-
-  // moments (the moment update after the LBGK equation, plus the energy)
-  const double n = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-  const double jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-  const double jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-  const double E = ((f[1] + f[2]) + (f[3] + f[4])) + 2.0 * ((f[5] + f[6]) + (f[7] + f[8]));
-  const double in = 1.0 / n;
-  const double ux = jx * in, uy = jy * in;
-  double J2, J4;
-  if (STAT == STAT_FD) {
-    J2 = 1.5 * (E * in - (ux * ux + uy * uy));  // 3 (E/n - u^2)/D
-    int cl;
-    const double xx = invert_j2(J2, L, &cl);
-    J4 = j4_of(fd_eval(xx));
-  } else {
-    J2 = FixedJ<STAT>::j2;
-    J4 = FixedJ<STAT>::j4;
-  }
-  double fe[9];
-  feq_f64(n, ux, uy, J2, J4, fe);
-  const double w = P.omega;
+  do {
+    const int p = nprob == 1 ? 0 : find_problem(probs, nprob, tile);
+    const ProbDev& P = probs[p];
+    const int lt = tile - (int)P.tile_begin;
+    const int ty = lt / P.tiles_x;
+    const int x = (lt - ty * P.tiles_x) * kTileX + (int)threadIdx.x;
+    if (x >= P.nx) continue;
+    const int y1 = min(ty * TY + TY, P.ny);
+#pragma unroll 1
+    for (int y = ty * TY; y < y1; ++y) {
+      const PullIdx q = pull_index(P, x, y);
+      double f[9];
+      pull9(fin, plane, q, x, f);
+      // moments (the moment update after the LBGK equation, plus the energy)
+      const double n = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+      const double jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+      const double jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+      const double E = ((f[1] + f[2]) + (f[3] + f[4])) + 2.0 * ((f[5] + f[6]) + (f[7] + f[8]));
+      const double in = 1.0 / n;
+      const double ux = jx * in, uy = jy * in;
+      double J2, J4;
+      if (STAT == STAT_FD) {
+        J2 = 1.5 * (E * in - (ux * ux + uy * uy));  // 3 (E/n - u^2)/D
+        int cl;
+        const double xx = invert_j2(J2, L, &cl);
+        J4 = j4_of(fd_eval(xx));
+      } else {
+        J2 = FixedJ<STAT>::j2;
+        J4 = FixedJ<STAT>::j4;
+      }
+      double fe[9];
+      feq_f64(n, ux, uy, J2, J4, fe);
+      const double w = P.omega;
 #pragma unroll
-  for (int a = 0; a < 9; ++a) fout[a * plane + q.row + x] = fma(w, fe[a] - f[a], f[a]);
-  }
-}
-
-// ------------------------------------------------------------------ per-context setup
-
-__global__ void setup_kernel(InvLimits* out) {
-  InvLimits L;
-  L.x_lo = x_of_t(kTMax);
-  L.x_hi = x_of_t(kTMin);
-  L.j2_lo = j2_of(fd_eval(L.x_lo));
-  L.j2_hi = j2_of(fd_eval(L.x_hi));
-  *out = L;
-}
-
-// Deviation reference of each problem: J_2,ref from t_ref (or the closure's
-// constant), W^ref = w_a(J_2,ref) n_ref and n_ref (3/2 - J_2,ref).
-__global__ void ref_kernel(ProbDev* probs, int nprob, int stat) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= nprob) return;
-  ProbDev& P = probs[p];
-  double J2, J4;
-  if (stat == STAT_FD) {
-    if (P.n_ref > 0.0) closure_from_t<STAT_FD>(P.t_ref, J2, J4); else J2 = 1.5;
-  } else if (stat == STAT_T0) {
-    J2 = FixedJ<STAT_T0>::j2;
-  } else {
-    J2 = FixedJ<STAT_MB>::j2;
-  }
-  const double n = P.n_ref;
-  const double w0 = n * (1.0 - 5.0 * J2 / 9.0), ws = n * J2 / 9.0, wl = n * J2 / 36.0;
-  P.j2_ref = J2;
-  P.ndelta_ref = n * (1.5 - J2);
-  P.wref[0] = w0;
-  for (int a = 1; a <= 4; ++a) P.wref[a] = ws;
-  for (int a = 5; a <= 8; ++a) P.wref[a] = wl;
-  P.f.omega = (float)P.omega;
-  P.f.n_ref = (float)n;
-  P.f.ndelta_ref = (float)P.ndelta_ref;
-  P.f.wref[0] = (float)w0;
-  P.f.wref[1] = (float)ws;
-  P.f.wref[2] = (float)wl;
+      for (int a = 0; a < 9; ++a) fout[a * plane + q.row + x] = fma(w, fe[a] - f[a], f[a]);
+    }
+  } while (PERSIST && (tile += (int)gridDim.x) < ntiles);
 }
 
 // ------------------------------------------------------------------ storage traits
@@ -366,24 +328,6 @@ __global__ void __launch_bounds__(kMomThreads) moments_kernel(const T* __restric
 #pragma unroll
     for (int w = 0; w < kMomThreads / 32; ++w) s += sh[w][threadIdx.x];
     partials[(int64_t)blockIdx.x * kNPartial + threadIdx.x] = s;
-  }
-}
-
-// One block sums the per-block partials in a fixed order.
-__global__ void __launch_bounds__(256) reduce_partials_kernel(const double* __restrict__ partials, int64_t nblocks,
-                                                              double* __restrict__ out) {
-  __shared__ double sh[256];
-  for (int k = 0; k < kNPartial; ++k) {
-    double s = 0.0;
-    for (int64_t b = threadIdx.x; b < nblocks; b += 256) s += partials[b * kNPartial + k];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) out[k] = sh[0];
-    __syncthreads();
   }
 }
 

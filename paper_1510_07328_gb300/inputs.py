@@ -228,3 +228,17 @@ def perturb_populations(f: np.ndarray, seed: int, amp: float) -> np.ndarray:
     """Multiply populations by (1 + amp * U[-1, 1]) to leave equilibrium."""
     r = uniform(seed, f.size).reshape(f.shape)
     return f * (1.0 + amp * (2.0 * r - 1.0))
+
+
+def surrogate_init(seed: int = 11, hidden: int = 64) -> np.ndarray:
+    """Initial weights of the 2 -> H -> H -> 2 network (Glorot-uniform
+    weights, zero biases), order W1, b1, W2, b2, W3, b3."""
+    sizes = [(hidden, 2), (hidden, hidden), (2, hidden)]
+    out = []
+    off = 0
+    for (fo, fi) in sizes:
+        a = math.sqrt(6.0 / (fi + fo))
+        out.append(a * (2.0 * uniform(seed, fo * fi, offset=off) - 1.0))
+        off += fo * fi
+        out.append(np.zeros(fo))
+    return np.concatenate(out).astype(np.float32)

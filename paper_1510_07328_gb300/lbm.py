@@ -50,6 +50,20 @@ class lbm_riemann_desc(C.Structure):
                 ("field_on_device", C.c_int32)]
 
 
+class lbm_tiling(C.Structure):
+    _fields_ = [("rows_per_tile", C.c_int32), ("ctas", C.c_int32), ("ms_per_step", C.c_double)]
+
+
+class lbm_train_cfg(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("lr_final", C.c_float)]
+
+
+class lbm_train_report(C.Structure):
+    _fields_ = [("iterations", C.c_int64), ("loss_first", C.c_double), ("loss_last", C.c_double),
+                ("val_rmse_lnT", C.c_double), ("val_rmse_mu", C.c_double), ("val_max_rel_x", C.c_double),
+                ("seconds", C.c_double)]
+
+
 class lbm_diag(C.Structure):
     _fields_ = [("sum_n", C.c_double), ("sum_jx", C.c_double), ("sum_jy", C.c_double), ("sum_E", C.c_double),
                 ("clamped", C.c_int64), ("nonfinite", C.c_int64)]
@@ -73,6 +87,16 @@ def _load():
         "lbm_last_error": (C.c_char_p, [V]),
         "lbm_launch_count": (C.c_int64, [V]),
         "lbm_conservation_sums_static": (C.c_int, [V, C.c_int32, C.c_int32, C.c_int32, V, V]),
+        "lbm_set_tiling": (C.c_int, [V, C.c_int32, C.c_int32]),
+        "lbm_get_tiling": (C.c_int, [V, C.POINTER(lbm_tiling)]),
+        "lbm_autotune": (C.c_int, [V, C.c_int32, C.POINTER(lbm_tiling)]),
+        "lbm_surrogate_targets": (C.c_int, [V, V, C.c_int64, C.c_int32, V, V, V]),
+        "lbm_surrogate_loss_grad": (C.c_int, [V, V, V, C.c_int64, V, C.POINTER(C.c_double), V]),
+        "lbm_surrogate_train": (C.c_int, [V, V, C.c_int64, V, V, C.c_int64, C.c_int32, C.POINTER(lbm_train_cfg),
+                                          V, C.POINTER(lbm_train_report), V]),
+        "lbm_surrogate_eval": (C.c_int, [V, V, V, C.c_int64, V, V, C.c_int32, V]),
+        "lbm_surrogate_load": (C.c_int, [V, V]),
+        "lbm_surrogate_stats": (C.c_int, [V, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -84,7 +108,10 @@ def _load():
 LIB = _load()
 EXPORTS = ("lbm_create", "lbm_init_riemann", "lbm_step", "lbm_moments", "lbm_get_populations",
            "lbm_set_populations", "lbm_destroy", "lbm_last_error", "lbm_launch_count",
-           "lbm_conservation_sums_static")
+           "lbm_conservation_sums_static", "lbm_set_tiling", "lbm_get_tiling", "lbm_autotune",
+           "lbm_surrogate_targets", "lbm_surrogate_loss_grad", "lbm_surrogate_train", "lbm_surrogate_eval",
+           "lbm_surrogate_load", "lbm_surrogate_stats")
+NPARAM = 4482
 
 
 class LbmError(RuntimeError):
@@ -182,6 +209,101 @@ def lbm_launch_count(ctx) -> int:
     return int(LIB.lbm_launch_count(ctx))
 
 
+def lbm_set_tiling(ctx, rows_per_tile: int, ctas: int = 0):
+    _check(LIB.lbm_set_tiling(ctx, int(rows_per_tile), int(ctas)), ctx)
+
+
+def lbm_get_tiling(ctx) -> dict:
+    t = lbm_tiling()
+    _check(LIB.lbm_get_tiling(ctx, C.byref(t)), ctx)
+    return {"rows_per_tile": t.rows_per_tile, "ctas": t.ctas}
+
+
+def lbm_autotune(ctx, steps_per_candidate: int = 4) -> dict:
+    t = lbm_tiling()
+    _check(LIB.lbm_autotune(ctx, int(steps_per_candidate), C.byref(t)), ctx)
+    return {"rows_per_tile": t.rows_per_tile, "ctas": t.ctas, "ms_per_step": t.ms_per_step}
+
+
+def _f32(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data
+
+
+def _f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data
+
+
+def _status(st, what):
+    if st != LBM_OK:
+        raise LbmError(st, what)
+
+
+def lbm_surrogate_targets(n, t):
+    """(features, targets) of the exact forward map for host arrays n, t."""
+    n, pn = _f64(n)
+    t, pt = _f64(t)
+    feat = np.empty((len(n), 2), dtype=np.float32)
+    targ = np.empty((len(n), 2), dtype=np.float32)
+    _status(LIB.lbm_surrogate_targets(pn, pt, len(n), 0, feat.ctypes.data, targ.ctypes.data, None),
+            "lbm_surrogate_targets")
+    return feat, targ
+
+
+def lbm_surrogate_loss_grad(params, feat, targ):
+    p, pp = _f32(params)
+    f, pf = _f32(feat)
+    g_, pg = _f32(targ)
+    grad = np.empty(NPARAM, dtype=np.float32)
+    loss = C.c_double()
+    _status(LIB.lbm_surrogate_loss_grad(pp, pf, pg, f.shape[0], grad.ctypes.data, C.byref(loss), None),
+            "lbm_surrogate_loss_grad")
+    return loss.value, grad
+
+
+def lbm_surrogate_train(params, n, t, n_val=None, t_val=None, epochs=32, batch=1024, lr=5e-3, lr_final=1e-6,
+                        stream=None):
+    """Train from initial params (not modified); returns (params, report)."""
+    p = np.array(params, dtype=np.float32, copy=True)
+    n, pn = _f64(n)
+    t, pt = _f64(t)
+    if n_val is not None:
+        nv, pnv = _f64(n_val)
+        tv, ptv = _f64(t_val)
+        cv = len(nv)
+    else:
+        pnv = ptv = None
+        cv = 0
+    cfg = lbm_train_cfg(int(epochs), int(batch), float(lr), float(lr_final))
+    rep = lbm_train_report()
+    _status(LIB.lbm_surrogate_train(pn, pt, len(n), pnv, ptv, cv, 0, C.byref(cfg), p.ctypes.data, C.byref(rep),
+                                    C.c_void_p(stream or 0)), "lbm_surrogate_train")
+    return p, {k: getattr(rep, k) for k, _ in lbm_train_report._fields_}
+
+
+def lbm_surrogate_eval(params, n, e):
+    p, pp = _f32(params)
+    n, pn = _f64(n)
+    e, pe = _f64(e)
+    T = np.empty(len(n))
+    mu = np.empty(len(n))
+    _status(LIB.lbm_surrogate_eval(pp, pn, pe, len(n), T.ctypes.data, mu.ctypes.data, 0, None), "lbm_surrogate_eval")
+    return T, mu
+
+
+def lbm_surrogate_load(ctx, params):
+    p, pp = _f32(params)
+    _check(LIB.lbm_surrogate_load(ctx, pp), ctx)
+
+
+def lbm_surrogate_stats(ctx) -> dict:
+    fb = C.c_int64()
+    ev = C.c_int64()
+    _check(LIB.lbm_surrogate_stats(ctx, C.byref(fb), C.byref(ev)), ctx)
+    return {"fallbacks": fb.value, "evaluations": ev.value}
+
+
 def lbm_conservation_sums_static(f, nx: int, ny: int, out, stat="fd", stream=None):
     """Conservation totals of device FP64 populations f[9][ny][nx] into the
     device array out (6 doubles), without any device allocation: for callers
@@ -196,7 +318,8 @@ def lbm_conservation_sums_static(f, nx: int, ny: int, out, stat="fd", stream=Non
 class Lattice:
     """One context over a list of problems (``inputs.Problem`` objects)."""
 
-    def __init__(self, problems, stat="fd", prec="f64", stream=None, t_ref=None, n_ref=None):
+    def __init__(self, problems, stat="fd", prec="f64", stream=None, t_ref=None, n_ref=None, inv="exact",
+                 surrogate=None):
         self.problems = list(problems)
         descs = []
         for p in self.problems:
@@ -204,8 +327,10 @@ class Lattice:
             nr = n_ref if n_ref is not None else float(np.mean(p.n))
             descs.append(dict(nx=p.nx, ny=p.ny, tau=p.tau, bc_x=p.bc_x, bc_y=p.bc_y, n_ref=nr,
                               t_ref=min(max(tr, 1e-3), 10.0)))
-        self.ctx = lbm_create(descs, stat, prec, stream=stream)
+        self.ctx = lbm_create(descs, stat, prec, inv=inv, stream=stream)
         self.stat = stat
+        if surrogate is not None:
+            lbm_surrogate_load(self.ctx, surrogate)
 
     def init(self, index=None, fields_on_device=None):
         for i, p in enumerate(self.problems):

@@ -1,0 +1,149 @@
+"""The learned Fermi-Dirac inversion: training kernels, gradients, inference
+and the learned step, against the FP64 oracle.
+
+Inputs flow one way only: features and targets come from the oracle's exact
+forward map (oracle/mlp.py) and are handed to the library as FP32.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import lbm as olbm
+from oracle import mlp
+from paper_1510_07328_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_1510_07328_gb300 import build
+
+    build.build()
+    from paper_1510_07328_gb300 import lbm
+
+    return lbm
+
+
+@pytest.fixture(scope="module")
+def trained(L):
+    n, t = inputs.surrogate_set(1 << 19, seed=4)
+    nv, tv = inputs.surrogate_set(8192, seed=5)
+    p, rep = L.lbm_surrogate_train(inputs.surrogate_init(11), n, t, nv, tv, epochs=16, batch=1024)
+    return p, rep
+
+
+def oracle_batch(count, seed):
+    n, t = inputs.surrogate_set(count, seed=seed)
+    _, e, Y, T, mu = mlp.targets_from_state(n, t)
+    X = mlp.features(n, e)
+    return n, e, X.astype(np.float32), Y.astype(np.float32), T, mu
+
+
+def test_targets_match_oracle(L):
+    n, t = inputs.surrogate_set(4096, seed=21)
+    feat, targ = L.lbm_surrogate_targets(n, t)
+    _, e, Y, _, _ = mlp.targets_from_state(n, t)
+    np.testing.assert_allclose(feat, mlp.features(n, e), atol=2e-7)
+    np.testing.assert_allclose(targ, Y, atol=4e-7)
+
+
+def test_gradient_against_oracle(L):
+    p = inputs.surrogate_init(11)
+    _, _, X, Y, _, _ = oracle_batch(1000, 22)
+    loss_g, grad_g = L.lbm_surrogate_loss_grad(p, X, Y)
+    loss_o, grad_o = mlp.loss_and_grad(p.astype(np.float64), X.astype(np.float64), Y.astype(np.float64))
+    assert abs(loss_g - loss_o) <= 2e-6 * loss_o
+    assert np.abs(grad_g - grad_o).max() <= 2e-5 * np.abs(grad_o).max()
+
+
+def test_training_deterministic_and_learns(L, trained):
+    p, rep = trained
+    assert rep["loss_last"] < 0.002 * rep["loss_first"]
+    n, t = inputs.surrogate_set(1 << 19, seed=4)
+    nv, tv = inputs.surrogate_set(8192, seed=5)
+    p2, _ = L.lbm_surrogate_train(inputs.surrogate_init(11), n, t, nv, tv, epochs=16, batch=1024)
+    assert np.array_equal(p, p2)
+    # validation error of the trained network, measured with the oracle network
+    _, e, _, _, _ = mlp.targets_from_state(nv, tv)
+    T, mu = mlp.predict(p.astype(np.float64), nv, e)
+    _, _, _, T_true, mu_true = mlp.targets_from_state(nv, tv)
+    rmse_lnT = float(np.sqrt(np.mean((np.log(T) - np.log(T_true)) ** 2)))
+    assert abs(rmse_lnT - rep["val_rmse_lnT"]) < 1e-3 + 0.1 * rep["val_rmse_lnT"]
+    assert rmse_lnT < 0.01
+
+
+def test_eval_matches_oracle_network(L, trained):
+    p, _ = trained
+    n, e, _, _, _, _ = oracle_batch(2048, 23)
+    T_g, mu_g = L.lbm_surrogate_eval(p, n, e)
+    T_o, mu_o = mlp.predict(p.astype(np.float64), n, e)
+    np.testing.assert_allclose(T_g, T_o, rtol=2e-5)
+    np.testing.assert_allclose(mu_g, mu_o, rtol=2e-5, atol=1e-7)
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+def test_learned_step_parity(L, trained, prec):
+    """The learned step reaches the exact inversion's result (to the FP32
+    tolerance of test_gpu_reduced): accepted cells are polished to it, the
+    others fall back."""
+    p_net, _ = trained
+    prob = inputs.random_field(300, 5, 61, tau=0.7, bc_x="bounceback", t_lo=0.02, t_hi=0.25)
+    n_ref, t_ref = 0.95, 0.05
+    from oracle import fd, gpoly
+
+    W = gpoly.weights(2, n_ref, float(fd.j2_of_x(fd.x_of_t(np.array([t_ref])))[0]))[:, None, None]
+    f = inputs.perturb_populations(olbm.init_equilibrium(prob.n, prob.ux, prob.uy, prob.t), 71, 0.002)
+    par = olbm.Params(tau=prob.tau, bc_x=prob.bc_x, bc_y=prob.bc_y)
+    lat = L.Lattice([prob], prec=prec, inv="surrogate", surrogate=p_net, n_ref=n_ref, t_ref=t_ref)
+    u = {"f32": 2.0 ** -24, "bf16": 2.0 ** -8}[prec]
+    for _ in range(2):
+        lat.set_populations(f)
+        lat.step(1)
+        got = lat.populations(0)
+        g_in = np.abs(f - W).max()
+        f = olbm.step(f, par)
+        tol = 8 * u * max(g_in, np.abs(f - W).max()) + 4e-6 * np.abs(f).max()
+        assert np.abs(got - f).max() <= tol
+    st = L.lbm_surrogate_stats(lat.ctx)
+    lat.close()
+    assert st["evaluations"] == 2 * prob.cells
+    assert 0 <= st["fallbacks"] <= st["evaluations"]
+
+
+def test_learned_inversion_against_exact_path(L, trained):
+    """What the network gains over the method without it: fields after 10
+    steps agree with the exact-inversion path to FP32 accuracy; the fallback
+    fraction and the time of both paths are printed (the network costs about
+    4.5 k FMA per cell, the exact inversion a few hundred instructions)."""
+    import torch
+
+    p_net, _ = trained
+    prob = inputs.random_field(512, 128, 62, tau=0.8, u_max=0.01, n_lo=0.95, n_hi=1.05, t_lo=0.03, t_hi=0.2)
+    res = {}
+    for inv in ("exact", "surrogate"):
+        lat = L.Lattice([prob], prec="f32", inv=inv, surrogate=p_net if inv == "surrogate" else None,
+                        n_ref=1.0, t_ref=0.1)
+        lat.init()
+        lat.step(2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lat.step(8)
+        e1.record()
+        torch.cuda.synchronize()
+        res[inv] = (lat.fields(0), e0.elapsed_time(e1) / 8)
+        if inv == "surrogate":
+            st = L.lbm_surrogate_stats(lat.ctx)
+        lat.close()
+    fa, fb = res["exact"][0], res["surrogate"][0]
+    assert np.abs(fa["n"] - fb["n"]).max() < 1e-5
+    assert np.abs(fa["ux"] - fb["ux"]).max() < 1e-5
+    frac = st["fallbacks"] / max(st["evaluations"], 1)
+    print(f"learned inversion: fallback fraction {frac:.4f}, ms/step exact {res['exact'][1]:.4f}, "
+          f"learned {res['surrogate'][1]:.4f}")
+    assert frac < 0.1
