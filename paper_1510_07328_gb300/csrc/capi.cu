@@ -192,7 +192,7 @@ void launch_init_t(lbm_ctx* c, const ProbDev& P, const InitDesc& d) {
 
 template <class T, int STAT>
 void launch_moments_t(lbm_ctx* c, const ProbDev& P, double* o[6], unsigned g) {
-  moments_kernel<T, STAT><<<g, kMomThreads, 0, c->stream>>>((const T*)c->buf[c->cur], P, c->plane, c->lim, o[0], o[1],
+  moments_kernel<T, STAT><<<g, kMomThreads, 0, c->stream>>>((const T*)c->buf[c->cur], P, c->plane, c->lim, c->limf, o[0], o[1],
                                                              o[2], o[3], o[4], o[5], c->partials);
 }
 

@@ -54,6 +54,14 @@ __device__ __forceinline__ void fd_poly(double x, double& p2, double& p3, double
   p4 = s * s * (1.0 / 24.0) + kPi2 * s * (1.0 / 12.0) + 7.0 * kPi2 * kPi2 / 360.0;
 }
 
+// 1/k, k = 1..48, for the series terms (warp-uniform reads).
+static __constant__ double c_inv_k64[49] = {
+    0.0,       1.0 / 1,  1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,  1.0 / 7,  1.0 / 8,  1.0 / 9,
+    1.0 / 10,  1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15, 1.0 / 16, 1.0 / 17, 1.0 / 18, 1.0 / 19,
+    1.0 / 20,  1.0 / 21, 1.0 / 22, 1.0 / 23, 1.0 / 24, 1.0 / 25, 1.0 / 26, 1.0 / 27, 1.0 / 28, 1.0 / 29,
+    1.0 / 30,  1.0 / 31, 1.0 / 32, 1.0 / 33, 1.0 / 34, 1.0 / 35, 1.0 / 36, 1.0 / 37, 1.0 / 38, 1.0 / 39,
+    1.0 / 40,  1.0 / 41, 1.0 / 42, 1.0 / 43, 1.0 / 44, 1.0 / 45, 1.0 / 46, 1.0 / 47, 1.0 / 48};
+
 // S_2, S_3, S_4 at y = e^{-a}, a >= 0.
 static __device__ __noinline__ void fd_alt_series(double a, double& s2, double& s3, double& s4) {
   const double y = exp(-a);
@@ -62,7 +70,7 @@ static __device__ __noinline__ void fd_alt_series(double a, double& s2, double& 
     double yk = y, sg = 1.0;
 #pragma unroll 1
     for (int k = 1; k <= 48; ++k) {
-      const double ik = 1.0 / (double)k;
+      const double ik = c_inv_k64[k];
       const double t2 = yk * ik * ik, t3 = t2 * ik, t4 = t3 * ik;
       s2 = fma(sg, t2, s2);
       s3 = fma(sg, t3, s3);

@@ -5,13 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fd_device_f32.cuh"
 #include "lbm_kernels.cuh"
 
 namespace lbm {
-
-struct InvLimitsF {
-  float x_lo, x_hi, j2_lo, j2_hi;
-};
 
 struct StepArgs {
   const void* in;

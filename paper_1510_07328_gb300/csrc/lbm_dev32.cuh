@@ -16,14 +16,12 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include "fd_device_f32.cuh"
 #include "launch.h"
 #include "lbm_kernels.cuh"
 #include "surrogate.cuh"
 
 namespace lbm {
-
-constexpr float kPi2f = 9.8696044010893586f;
-constexpr float kXDegF = 17.0f;  // e^-17 = 4e-8: S_n tails below FP32 resolution
 
 template <class T>
 struct Dev;
@@ -37,242 +35,6 @@ struct Dev<__nv_bfloat16> {
   __device__ static __forceinline__ float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
   __device__ static __forceinline__ __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
 };
-
-struct FD5f {
-  float f0, f1, f2, f3, f4;
-};
-
-// 1/k for the series terms (k = 1..12), read warp-uniformly.
-__constant__ float c_inv_k[13] = {0.f,     1.f,         0.5f,   1.f / 3.f, 0.25f,      0.2f,       1.f / 6.f,
-                                  1.f / 7.f, 0.125f, 1.f / 9.f, 0.1f,  1.f / 11.f, 1.f / 12.f};
-
-// FP32 f_0..f_4 (same expansions as the FP64 functions; FP32 term counts).
-// For a = |x| >= 2 the series S_n(e^{-a}) needs ceil(17/a) terms: its tail is
-// then below e^{-17} = 4e-8, under FP32 resolution of f_n >= 1.
-__device__ __forceinline__ FD5f fd_eval_f(float x) {
-  FD5f r;
-  const float a = fabsf(x);
-  const float em = __expf(-a);
-  const float r1 = __fdividef(1.0f, 1.0f + em);
-  r.f0 = x >= 0.0f ? r1 : em * r1;
-  const float s = x * x;
-  const float p2 = 0.5f * s + kPi2f / 6.0f;
-  const float p3 = x * (s + kPi2f) * (1.0f / 6.0f);
-  const float p4 = s * s * (1.0f / 24.0f) + kPi2f * s * (1.0f / 12.0f) + 7.0f * kPi2f * kPi2f / 360.0f;
-  if (x >= kXDegF) {
-    r.f1 = x + __logf(1.0f + em);
-    r.f2 = p2; r.f3 = p3; r.f4 = p4;
-    return r;
-  }
-  float s2 = 0.f, s3 = 0.f, s4 = 0.f;
-  const float y = em;
-  if (a >= 2.0f) {
-    r.f1 = fmaxf(x, 0.0f) + __logf(1.0f + em);
-    const int K = min(9, (int)(kXDegF / a) + 1);
-    float yk = y, sg = 1.0f;
-#pragma unroll 1
-    for (int k = 1; k <= K; ++k) {
-      const float ik = c_inv_k[k];
-      const float t2 = yk * ik * ik, t3 = t2 * ik, t4 = t3 * ik;
-      s2 = fmaf(sg, t2, s2); s3 = fmaf(sg, t3, s3); s4 = fmaf(sg, t4, s4);
-      yk *= y;
-      sg = -sg;
-    }
-  } else {
-    r.f1 = fmaxf(x, 0.0f) + log1pf(em);
-    // Cohen, Rodriguez Villegas, Zagier Algorithm 1, N = 12 ((3+sqrt 8)^12 ~ 1.5e9)
-    const int N = 12;
-    const float d = 0.5f * (1.5209e9f + 1.0f / 1.5209e9f);
-    float b = -1.0f, c = -d, yk = y;
-#pragma unroll 1
-    for (int k = 0; k < N; ++k) {
-      c = b - c;
-      const float ik = c_inv_k[k + 1];
-      const float a2 = yk * ik * ik, a3 = a2 * ik, a4 = a3 * ik;
-      s2 = fmaf(c, a2, s2); s3 = fmaf(c, a3, s3); s4 = fmaf(c, a4, s4);
-      b = (float)(k + N) * (float)(k - N) * b / (((float)k + 0.5f) * (float)(k + 1));
-      yk *= y;
-    }
-    s2 /= d; s3 /= d; s4 /= d;
-  }
-  if (x > 0.0f) {
-    r.f2 = p2 - s2; r.f3 = p3 + s3; r.f4 = p4 - s4;
-  } else {
-    r.f2 = s2; r.f3 = s3; r.f4 = s4;
-  }
-  return r;
-}
-
-// Single-instruction approximations (MUFU) for the inversion: about 1-2 ulp,
-// far inside its FP32 error budget.
-__device__ __forceinline__ float rcp_a(float v) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
-  return r;
-}
-__device__ __forceinline__ float sqrt_a(float v) {
-  float r;
-  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
-  return r;
-}
-__device__ __forceinline__ float expm_a(float v) {  // e^{-v}
-  float r;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-1.4426950408889634f * v));
-  return r;
-}
-
-// P_2, P_3, P_4 of the inversion formula at x (the degenerate parts of f_n).
-__device__ __forceinline__ void fd_poly_f(float x, float& p2, float& p3, float& p4) {
-  const float s = x * x;
-  p2 = 0.5f * s + kPi2f / 6.0f;
-  p3 = x * (s + kPi2f) * (1.0f / 6.0f);
-  p4 = s * s * (1.0f / 24.0f) + kPi2f * s * (1.0f / 12.0f) + 7.0f * kPi2f * kPi2f / 360.0f;
-}
-
-// Large root s = x^2 of 6 delta s^2 - (3 pi^2 - 6 delta pi^2) s + pi^4 = 0:
-// the degenerate form 3/2 - J_2 = pi^2 (3 s - pi^2)/(6 s (s + pi^2)).
-__device__ __forceinline__ float deg_root_f(float delta) {
-  const float A = 6.0f * delta, B = 3.0f * kPi2f - 6.0f * delta * kPi2f, C = kPi2f * kPi2f;
-  return (B + sqrt_a(fmaxf(B * B - 4.0f * A * C, 0.0f))) * rcp_a(2.0f * A);
-}
-
-// J_4 in the degenerate regime from s = x^2 (S_n tails dropped):
-// J_4 = P_3^2/(P_2 P_4) = 60 s (s + pi^2)^2 / ((3 s + pi^2)(15 s^2 + 30 pi^2 s + 7 pi^4)).
-__device__ __forceinline__ float j4_degenerate_f(float s) {
-  const float sp = s + kPi2f;
-  return 60.0f * s * sp * sp *
-         rcp_a((3.0f * s + kPi2f) * (15.0f * s * s + 30.0f * kPi2f * s + 7.0f * kPi2f * kPi2f));
-}
-
-// One fixed-point pass that folds the leading tails into the degenerate
-// root.  With y = e^{-x} the first series terms change f_1, f_2, f_3 by
-// +y, -y, +y, hence J_2 by -J_2 y (2/P_2 + 1/x + 1/P_3); the pass solves the
-// degenerate quadratic for delta minus that change at the current x.  The
-// remaining error is O(y^2): below FP32 resolution of J_4 for x >= 9 after one
-// pass and x >= 7 after two.
-__device__ __forceinline__ float tail_pass_f(float delta, float x) {
-  const float y = expm_a(x);
-  float p2, p3, p4;
-  fd_poly_f(x, p2, p3, p4);
-  const float ip2 = rcp_a(p2), ip3 = rcp_a(p3), ix = rcp_a(x);
-  const float J2d = p2 * p2 * ix * ip3;
-  const float c = J2d * y * (2.0f * ip2 + ix + ip3);
-  return sqrt_a(deg_root_f(delta - c));
-}
-
-// J_4 with the first two series terms of f_2, f_3, f_4 (error O(y^3)).
-__device__ __forceinline__ float j4_tail_f(float x) {
-  const float y = expm_a(x);
-  float p2, p3, p4;
-  fd_poly_f(x, p2, p3, p4);
-  const float f2 = p2 - y * (1.0f - 0.25f * y);
-  const float f3 = p3 + y * (1.0f - 0.125f * y);
-  const float f4 = p4 - y * (1.0f - 0.0625f * y);
-  return f3 * f3 * rcp_a(f2 * f4);
-}
-
-// f_0..f_4 for x >= 4 (y = e^{-x} <= 0.019): three series terms in Horner
-// form (the fourth is below 2e-10 of f_2) and log1p(y) to y^4.
-__device__ __forceinline__ FD5f fd_eval_deg_f(float x) {
-  FD5f r;
-  const float y = expm_a(x);
-  float p2, p3, p4;
-  fd_poly_f(x, p2, p3, p4);
-  const float s2 = y * (1.0f + y * (-0.25f + y * (1.0f / 9.0f)));
-  const float s3 = y * (1.0f + y * (-0.125f + y * (1.0f / 27.0f)));
-  const float s4 = y * (1.0f + y * (-0.0625f + y * (1.0f / 81.0f)));
-  r.f0 = rcp_a(1.0f + y);
-  r.f1 = x + y * (1.0f + y * (-0.5f + y * (1.0f / 3.0f - 0.25f * y)));
-  r.f2 = p2 - s2;
-  r.f3 = p3 + s3;
-  r.f4 = p4 - s4;
-  return r;
-}
-
-// J_4 from delta = 3/2 - J_2 in FP32 (the exact inversion, to FP32
-// resolution; *xout receives x).
-//  * non-finite input: propagated at once;
-//  * J_2 beyond the clamp interval: x at the nearest end;
-//  * degenerate regime (delta < 0.15, x > 4.2): the quadratic root; closed
-//    form J_4 for x >= 17; one tail pass for x >= 9, two for x >= 7; below
-//    that Newton steps on J_2(x) from the second pass, each with one
-//    evaluation of f_0..f_4, stopping when the step is below 5e-4 x and
-//    returning x + dx and J_4 + J_4' dx (second-order remainder < 1e-7).
-//    J_2' = J_2 (2 f_1/f_2 - f_0/f_1 - f_2/f_3), J_4' = J_4 (2 f_2/f_3 -
-//    f_1/f_2 - f_3/f_4), from d f_n/dx = f_{n-1};
-//  * otherwise (J_2 < 4/3): safeguarded Newton with the general FP32
-//    evaluation, at most 24 evaluations.
-__device__ __forceinline__ float j4_from_delta_f(float delta, const InvLimitsF& L, float* xout) {
-  const float J2 = 1.5f - delta;
-  if (!(J2 == J2)) {  // non-finite state: propagate without iterating
-    *xout = J2;
-    return J2;
-  }
-  if (!(J2 < L.j2_hi)) {
-    *xout = L.x_hi;
-    return j4_degenerate_f(L.x_hi * L.x_hi);
-  }
-  if (J2 <= L.j2_lo) {
-    const FD5f f = fd_eval_f(L.x_lo);
-    *xout = L.x_lo;
-    return f.f3 * f.f3 * rcp_a(f.f2 * f.f4);
-  }
-  if (delta < 0.15f) {
-    const float s = deg_root_f(delta);
-    if (s >= kXDegF * kXDegF) {
-      *xout = sqrt_a(s);
-      return j4_degenerate_f(s);
-    }
-    float x = tail_pass_f(delta, sqrt_a(s));
-    if (x >= 9.0f) {
-      *xout = x;
-      return j4_tail_f(x);
-    }
-    x = tail_pass_f(delta, x);
-    if (x >= 7.0f) {
-      *xout = x;
-      return j4_tail_f(x);
-    }
-#pragma unroll 1
-    for (int it = 0; it < 4; ++it) {
-      const FD5f f = fd_eval_deg_f(x);
-      const float i1 = rcp_a(f.f1), i2 = rcp_a(f.f2), i3 = rcp_a(f.f3), i4 = rcp_a(f.f4);
-      const float j = f.f2 * f.f2 * i1 * i3;
-      const float dj = j * (2.0f * f.f1 * i2 - f.f0 * i1 - f.f2 * i3);
-      const float dx = (J2 - j) * rcp_a(dj);
-      const float J4 = f.f3 * f.f3 * i2 * i4;
-      if (fabsf(dx) < 5e-4f * x || it == 3) {
-        const float dJ4 = J4 * (2.0f * f.f2 * i3 - f.f1 * i2 - f.f3 * i4);
-        *xout = x + dx;
-        return J4 + dJ4 * dx;
-      }
-      x += dx;
-    }
-  }
-  float x = 1.0f, lo = L.x_lo, hi = 6.0f;  // J_2(6) = 1.40 > 4/3: the root lies below
-  float J4 = 0.0f;
-#pragma unroll 1
-  for (int it = 0; it < 24; ++it) {
-    const FD5f f = fd_eval_f(x);
-    const float i1 = rcp_a(f.f1), i2 = rcp_a(f.f2), i3 = rcp_a(f.f3), i4 = rcp_a(f.f4);
-    const float j = f.f2 * f.f2 * i1 * i3;
-    const float g = j - J2;
-    const float dj = j * (2.0f * f.f1 * i2 - f.f0 * i1 - f.f2 * i3);
-    const float dx = -g * rcp_a(dj);
-    J4 = f.f3 * f.f3 * i2 * i4;
-    if (g < 0.0f) lo = x; else hi = x;
-    if (fabsf(dx) < 5e-4f * fabsf(x) || it == 23) {
-      const float dJ4 = J4 * (2.0f * f.f2 * i3 - f.f1 * i2 - f.f3 * i4);
-      *xout = x + dx;
-      return J4 + dJ4 * dx;
-    }
-    float xn = x + dx;
-    if (!(xn > lo && xn < hi)) xn = 0.5f * (lo + hi);
-    x = xn;
-  }
-  *xout = x;
-  return J4;
-}
 
 // J_4 through the learned inversion: the network gives (T, mu) from (n, e),
 // e = 2 n J_2/3, hence x_0 = mu/T; one Newton step on J_2(x) = J_2 polishes

@@ -11,6 +11,7 @@
 #include <stdint.h>
 
 #include "fd_device.cuh"
+#include "fd_device_f32.cuh"
 
 namespace lbm {
 
@@ -96,6 +97,66 @@ __device__ __forceinline__ void closure_from_t(double t, double& J2, double& J4)
   }
 }
 
+// J_4 in the degenerate regime, FP64, from s = x^2 (tails below 4.3e-18 for
+// x >= 40): J_4 = 60 s (s + pi^2)^2 / ((3 s + pi^2)(15 s^2 + 30 pi^2 s + 7 pi^4)).
+__device__ __forceinline__ double j4_degenerate(double s) {
+  const double sp = s + kPi2;
+  return 60.0 * s * sp * sp / ((3.0 * s + kPi2) * (15.0 * s * s + 30.0 * kPi2 * s + 7.0 * kPi2 * kPi2));
+}
+
+// The FP64 step's inversion: J_4 (and x) for a measured J_2.
+//  * clamp interval, NaN and the degenerate regime x >= 40 (exact quadratic
+//    root, closed-form J_4) as in invert_j2;
+//  * otherwise the FP32 inversion gives x_f (about 1e-6 relative); at x_f one
+//    FP64 evaluation of f_0..f_4 gives the Newton step dx = (J_2 - J_2(x_f))/
+//    J_2'(x_f) and J_4 = J_4(x_f) + J_4'(x_f) dx, whose second-order remainder
+//    J_4'' dx^2/2 is below 1e-13; the step repeats (at most 4 evaluations)
+//    while |dx| > 1e-6 |x|.
+__device__ __forceinline__ double j4_fp64(double J2, const InvLimits& L, const InvLimitsF& Lf, double* xout,
+                                          int* clamped) {
+  *clamped = 0;
+  if (!(J2 == J2) || isinf(J2)) {
+    *xout = J2 - J2;
+    return *xout;
+  }
+  if (J2 >= L.j2_hi || J2 <= L.j2_lo) {
+    *clamped = 1;
+    const double x = J2 >= L.j2_hi ? L.x_hi : L.x_lo;
+    *xout = x;
+    return j4_of(fd_eval(x));
+  }
+  const double delta = 1.5 - J2;
+  if (delta < 0.1) {
+    const double A = 6.0 * delta, B = 3.0 * kPi2 - 6.0 * delta * kPi2, C = kPi2 * kPi2;
+    const double sq = (B + sqrt(fmax(B * B - 4.0 * A * C, 0.0))) / (2.0 * A);
+    if (sq >= kXDeg * kXDeg) {
+      *xout = fmin(sqrt(sq), L.x_hi);
+      return j4_degenerate(*xout * *xout);
+    }
+  }
+  float xf;
+  j4_from_delta_f((float)delta, Lf, &xf);
+  double x = (double)xf;
+  double J4 = 0.0;
+#pragma unroll 1
+  for (int it = 0; it < 4; ++it) {
+    const FD5 f = fd_eval(x);
+    const double i1 = 1.0 / f.f1, i2 = 1.0 / f.f2, i3 = 1.0 / f.f3, i4 = 1.0 / f.f4;
+    const double j = f.f2 * f.f2 * i1 * i3;
+    const double dj = j * (2.0 * f.f1 * i2 - f.f0 * i1 - f.f2 * i3);
+    const double dx = (J2 - j) / dj;
+    J4 = f.f3 * f.f3 * i2 * i4;
+    if (fabs(dx) <= 1e-6 * fabs(x) || it == 3) {
+      const double dJ4 = J4 * (2.0 * f.f2 * i3 - f.f1 * i2 - f.f3 * i4);
+      *xout = x + dx;
+      return J4 + dJ4 * dx;
+    }
+    x = fmin(fmax(x + dx, L.x_lo), L.x_hi);
+  }
+  *xout = x;
+  return J4;
+}
+
 // Pull indices of the nine populations of cell (x, y); a negative row or
 // column marks an off-lattice source (bounce-back from the opposite
 // population of the same cell).
@@ -137,7 +198,7 @@ __device__ __forceinline__ void pull9(const T* __restrict__ fin, int64_t plane, 
 template <int STAT, int TY, bool PERSIST>
 __global__ void __launch_bounds__(kTileX) stream_collide_f64(const double* __restrict__ fin, double* __restrict__ fout,
                                                              const ProbDev* __restrict__ probs, int nprob, int ntiles,
-                                                             int64_t plane, InvLimits L) {
+                                                             int64_t plane, InvLimits L, InvLimitsF Lf) {
   int tile = (int)blockIdx.x;
 #pragma unroll 1
   do {
@@ -164,8 +225,8 @@ __global__ void __launch_bounds__(kTileX) stream_collide_f64(const double* __res
       if (STAT == STAT_FD) {
         J2 = 1.5 * (E * in - (ux * ux + uy * uy));  // 3 (E/n - u^2)/D
         int cl;
-        const double xx = invert_j2(J2, L, &cl);
-        J4 = j4_of(fd_eval(xx));
+        double xx;
+        J4 = j4_fp64(J2, L, Lf, &xx, &cl);
       } else {
         J2 = FixedJ<STAT>::j2;
         J4 = FixedJ<STAT>::j4;
@@ -263,7 +324,7 @@ constexpr int kNPartial = 6;  // sum n, jx, jy, E, clamped, nonfinite
 
 template <class T, int STAT>
 __global__ void __launch_bounds__(kMomThreads) moments_kernel(const T* __restrict__ f, ProbDev P, int64_t plane,
-                                                              InvLimits L, double* __restrict__ on,
+                                                              InvLimits L, InvLimitsF Lf, double* __restrict__ on,
                                                               double* __restrict__ oux, double* __restrict__ ouy,
                                                               double* __restrict__ oT, double* __restrict__ omu,
                                                               double* __restrict__ ot, double* __restrict__ partials) {
@@ -285,9 +346,9 @@ __global__ void __launch_bounds__(kMomThreads) moments_kernel(const T* __restric
     int cl = 0;
     if (STAT == STAT_FD) {
       const double J2 = 1.5 * (E / n - (ux * ux + uy * uy));
-      const double xx = invert_j2(J2, L, &cl);
-      const FD5 F = fd_eval(xx);
-      t = 1.0 / F.f1;                  // t = T/T_F = 1/f_1(x)
+      double xx;
+      j4_fp64(J2, L, Lf, &xx, &cl);
+      t = 1.0 / (fmax(xx, 0.0) + log1p(exp(-fabs(xx))));  // t = T/T_F = 1/f_1(x)
       theta = n * t / (2.0 * kPi);     // theta = n t/(2 pi), T_F = n/(2 pi)
       mu = theta * xx;
     } else if (STAT == STAT_T0) {

@@ -9,10 +9,10 @@ template <int STAT, int TY>
 static void go(unsigned grid, cudaStream_t s, const StepArgs& a) {
   if ((int)grid < a.ntiles)
     stream_collide_f64<STAT, TY, true><<<grid, kTileX, 0, s>>>((const double*)a.in, (double*)a.out, a.probs, a.nprob,
-                                                               a.ntiles, a.plane, a.lim);
+                                                               a.ntiles, a.plane, a.lim, a.limf);
   else
     stream_collide_f64<STAT, TY, false><<<grid, kTileX, 0, s>>>((const double*)a.in, (double*)a.out, a.probs, a.nprob,
-                                                       a.ntiles, a.plane, a.lim);
+                                                       a.ntiles, a.plane, a.lim, a.limf);
 }
 
 template <int STAT>
