@@ -254,8 +254,16 @@ lbm_status lbm_surrogate_eval(const float* params, const double* n, const double
  * context, NULL, non-finite values), LBM_ENOMEM. */
 lbm_status lbm_surrogate_load(lbm_ctx* ctx, const float* params);
 
+/* Where the network's 64 x 64 hidden layer runs: on the tensor cores
+ * (tcgen05 MMA, FP16 operands, FP32 accumulation in tensor memory; the
+ * default) or on the FP32 pipe (FP32 throughout).  Drops captured graphs. */
+enum { LBM_SURROGATE_FP32_PIPE = 0, LBM_SURROGATE_TENSOR_CORES = 1 };
+lbm_status lbm_surrogate_engine(lbm_ctx* ctx, int32_t engine);
+
 /* Cells that went through the network, and those that fell back to the exact
- * inversion, since the context was created.  Synchronises. */
+ * inversion, since the context was created.  Synchronises.  Returns
+ * LBM_ETIMEOUT (counts still filled) if a tensor-core wait ever gave up; the
+ * cells concerned were served by the exact inversion. */
 lbm_status lbm_surrogate_stats(lbm_ctx* ctx, int64_t* fallbacks, int64_t* evaluations);
 
 /* lbm_conservation_sums_static - the paper has no counterpart to this call;

@@ -115,7 +115,9 @@ struct lbm_ctx {
   int64_t launches = 0;
   std::string err;
   MlpParams* surr = nullptr;               // host copy of the network (learned inversion)
-  unsigned long long* surr_count = nullptr;  // device: fallbacks, evaluations
+  unsigned long long* surr_count = nullptr;  // device: fallbacks, evaluations, tensor-core timeouts
+  void* w2h = nullptr;                       // device: W2 as FP16 in the canonical K-major layout
+  int surr_engine = LBM_SURROGATE_TENSOR_CORES;
 };
 
 namespace {
@@ -148,10 +150,14 @@ void launch_step(lbm_ctx* c, const void* in, void* out, cudaStream_t s) {
   StepArgs a{in, out, c->pd, c->nprob, (int)c->ntiles, c->plane, c->lim, c->limf};
   const unsigned grid = c->ctas > 0 ? (unsigned)std::min<int64_t>(c->ctas, c->ntiles) : (unsigned)c->ntiles;
   if (c->inv == LBM_INV_SURROGATE) {
-    if (c->prec == LBM_F32_DEV)
-      launch_step_surr_f32(c->rows, grid, s, a, c->surr_count, *c->surr);
-    else
-      launch_step_surr_bf16(c->rows, grid, s, a, c->surr_count, *c->surr);
+    const bool tcore = c->surr_engine == LBM_SURROGATE_TENSOR_CORES;
+    if (c->prec == LBM_F32_DEV) {
+      if (tcore) launch_step_surr_tc_f32(c->rows, grid, s, a, c->surr_count, c->w2h, *c->surr);
+      else launch_step_surr_f32(c->rows, grid, s, a, c->surr_count, *c->surr);
+    } else {
+      if (tcore) launch_step_surr_tc_bf16(c->rows, grid, s, a, c->surr_count, c->w2h, *c->surr);
+      else launch_step_surr_bf16(c->rows, grid, s, a, c->surr_count, *c->surr);
+    }
     return;
   }
   switch (c->prec) {
@@ -303,8 +309,9 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&ctx->lim_d, sizeof(InvLimits));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->diag_d, sizeof(double) * kNPartial);
   if (e == cudaSuccess && p->inv == LBM_INV_SURROGATE) {
-    e = cudaMalloc(&ctx->surr_count, 2 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->surr_count, 0, 2 * sizeof(unsigned long long), ctx->stream);
+    e = cudaMalloc(&ctx->surr_count, 3 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->surr_count, 0, 3 * sizeof(unsigned long long), ctx->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->w2h, sizeof(__half) * kH * kH);
   }
   if (e != cudaSuccess) return cleanup(LBM_ENOMEM, std::string("lbm_create: tables: ") + cudaGetErrorString(e));
   e = cudaMemcpyAsync(ctx->pd, ctx->ph.data(), sizeof(ProbDev) * ctx->nprob, cudaMemcpyHostToDevice, ctx->stream);
@@ -462,6 +469,25 @@ lbm_status lbm_surrogate_load(lbm_ctx* ctx, const float* params) {
   if (!ctx->surr) ctx->surr = new (std::nothrow) MlpParams();
   if (!ctx->surr) return fail(ctx, LBM_ENOMEM, "lbm_surrogate_load: host allocation failed");
   std::memcpy(ctx->surr->p, params, sizeof(float) * kNParam);
+  // W2 as FP16 in the canonical K-major layout of the tensor-core operand:
+  // element (n, k) at core (n/8, k/8) = ((k/8) * 8 + n/8) * 128 bytes, row n%8
+  std::vector<__half> w2(kH * kH);
+  for (int n = 0; n < kH; ++n)
+    for (int k = 0; k < kH; ++k) {
+      const size_t byte = ((size_t)(k / 8) * (kH / 8) + n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
+      w2[byte / 2] = __float2half_rn(params[kOW2 + kH * n + k]);
+    }
+  CK(cudaMemcpyAsync(ctx->w2h, w2.data(), sizeof(__half) * kH * kH, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  drop_graphs(ctx);
+  return LBM_OK;
+}
+
+lbm_status lbm_surrogate_engine(lbm_ctx* ctx, int32_t engine) {
+  if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_surrogate_engine: NULL context");
+  if (engine != LBM_SURROGATE_FP32_PIPE && engine != LBM_SURROGATE_TENSOR_CORES)
+    return fail(ctx, LBM_EINVAL, "lbm_surrogate_engine: bad engine");
+  ctx->surr_engine = engine;
   drop_graphs(ctx);
   return LBM_OK;
 }
@@ -469,11 +495,12 @@ lbm_status lbm_surrogate_load(lbm_ctx* ctx, const float* params) {
 lbm_status lbm_surrogate_stats(lbm_ctx* ctx, int64_t* fallbacks, int64_t* evaluations) {
   if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_surrogate_stats: NULL context");
   if (!ctx->surr_count) return fail(ctx, LBM_EINVAL, "lbm_surrogate_stats: not a learned-inversion context");
-  unsigned long long h[2] = {0, 0};
+  unsigned long long h[3] = {0, 0, 0};
   CK(cudaMemcpyAsync(h, ctx->surr_count, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   if (fallbacks) *fallbacks = (int64_t)h[0];
   if (evaluations) *evaluations = (int64_t)h[1];
+  if (h[2]) return fail(ctx, LBM_ETIMEOUT, "lbm_surrogate_stats: a tensor-core wait timed out (cells served exactly)");
   return LBM_OK;
 }
 
@@ -654,6 +681,7 @@ lbm_status lbm_destroy(lbm_ctx* ctx) {
   if (ctx->tmp) cudaFree(ctx->tmp);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
   if (ctx->surr_count) cudaFree(ctx->surr_count);
+  if (ctx->w2h) cudaFree(ctx->w2h);
   delete ctx->surr;
   delete ctx;
   return LBM_OK;

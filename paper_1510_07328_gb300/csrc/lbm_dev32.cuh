@@ -20,6 +20,7 @@
 #include "launch.h"
 #include "lbm_kernels.cuh"
 #include "surrogate.cuh"
+#include "tc_sm100.cuh"
 
 namespace lbm {
 
@@ -36,23 +37,14 @@ struct Dev<__nv_bfloat16> {
   __device__ static __forceinline__ __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
 };
 
-// J_4 through the learned inversion: the network gives (T, mu) from (n, e),
-// e = 2 n J_2/3, hence x_0 = mu/T; one Newton step on J_2(x) = J_2 polishes
-// it to x_1; the residual check evaluates f_0..f_4 at x_1 and accepts when the
-// remaining Newton correction dx is below 5e-4 x_1 (the acceptance of the
-// exact iteration), returning J_4(x_1) + J_4'(x_1) dx.  Otherwise *fallback is
-// set and the exact inversion runs.
-__device__ __forceinline__ float j4_surrogate_f(float n, float delta, const InvLimitsF& L, const MlpParams& W,
-                                                int* fallback) {
+// Polish of the learned inversion's x_0 = mu/T: one Newton step on
+// J_2(x) = J_2 to x_1; the residual check evaluates f_0..f_4 at x_1 and
+// accepts when the remaining Newton correction dx is below 5e-4 x_1 (the
+// acceptance of the exact iteration), returning J_4(x_1) + J_4'(x_1) dx.
+// Otherwise *fallback is set and the exact inversion runs.
+__device__ __forceinline__ float j4_polish_f(float x0, float delta, const InvLimitsF& L, int* fallback) {
   const float J2 = 1.5f - delta;
-  if (!(J2 == J2) || !(J2 < L.j2_hi) || J2 <= L.j2_lo) {  // non-finite or clamped: the exact path handles it
-    float xx;
-    return j4_from_delta_f(delta, L, &xx);
-  }
-  float y0, y1, T, mu;
-  mlp_forward_f(W, n, delta, y0, y1);  // e = 2 n J_2/3 enters as delta = 3/2 - J_2
-  mlp_outputs_to_state(y0, y1, T, mu);
-  float x = fminf(fmaxf(mu * rcp_a(T), L.x_lo), L.x_hi);
+  float x = fminf(fmaxf(x0, L.x_lo), L.x_hi);
 #pragma unroll 1
   for (int it = 0; it < 2; ++it) {
     const FD5f f = x >= 4.0f ? fd_eval_deg_f(x) : fd_eval_f(x);
@@ -73,6 +65,26 @@ __device__ __forceinline__ float j4_surrogate_f(float n, float delta, const InvL
   *fallback = 1;
   float xx;
   return j4_from_delta_f(delta, L, &xx);
+}
+
+// Cells the network handles: finite J_2 inside the clamp interval.
+__device__ __forceinline__ bool net_cell(float delta, const InvLimitsF& L) {
+  const float J2 = 1.5f - delta;
+  return J2 == J2 && J2 < L.j2_hi && J2 > L.j2_lo;
+}
+
+// J_4 through the learned inversion, network on the FP32 pipe (the network
+// gives (T, mu) from (n, e), e = 2 n J_2/3 entering as delta = 3/2 - J_2).
+__device__ __forceinline__ float j4_surrogate_f(float n, float delta, const InvLimitsF& L, const MlpParams& W,
+                                                int* fallback) {
+  if (!net_cell(delta, L)) {  // non-finite or clamped: the exact path handles it
+    float xx;
+    return j4_from_delta_f(delta, L, &xx);
+  }
+  float y0, y1, T, mu;
+  mlp_forward_f(W, n, delta, y0, y1);
+  mlp_outputs_to_state(y0, y1, T, mu);
+  return j4_polish_f(mu * rcp_a(T), delta, L, fallback);
 }
 
 // 32-bit in-plane pull offsets (every plane holds fewer than 2^31 cells);
@@ -110,35 +122,33 @@ __device__ __forceinline__ void pull9_32(const T* __restrict__ fin, int64_t plan
   v[8] = ld(8, q.rp, q.xm, 6);
 }
 
-// Collision of one cell from its pulled deviations g[9]; stores at `off`.
-template <class T, int STAT, bool SURR = false>
-__device__ __forceinline__ void collide_store_dev(const ProbDev& P, const float g[9], T* __restrict__ fout,
-                                                  int64_t plane, int off, const InvLimitsF& L,
-                                                  const MlpParams* W = nullptr, int* fallback = nullptr) {
+// Moments of one cell from its pulled deviations (FP32, deviation form).
+struct CellMom {
+  float dn, n, in, ux, uy, u2, X, delta;
+};
+
+__device__ __forceinline__ CellMom dev_moments(const ProbDev& P, const float g[9]) {
+  CellMom m;
   const float nref = P.f.n_ref, ndref = P.f.ndelta_ref;
-  const float dn = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+  m.dn = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
   const float jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
   const float jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
   const float G1 = g[0] - ((g[5] + g[6]) + (g[7] + g[8]));
-  const float n = nref + dn;
-  const float in = __fdividef(1.0f, n);
-  const float ux = jx * in, uy = jy * in;
-  const float u2 = ux * ux + uy * uy;
-  const float X = G1 + n * u2;
-  float J2, J4;
-  if (STAT == STAT_FD) {
-    const float delta = (ndref + 1.5f * X) * in;  // 3/2 - J_2
-    J2 = 1.5f - delta;
-    if (SURR) {
-      J4 = j4_surrogate_f(n, delta, L, *W, fallback);
-    } else {
-      float xx;
-      J4 = j4_from_delta_f(delta, L, &xx);
-    }
-  } else {
-    J2 = (float)FixedJ<STAT>::j2;
-    J4 = (float)FixedJ<STAT>::j4;
-  }
+  m.n = nref + m.dn;
+  m.in = __fdividef(1.0f, m.n);
+  m.ux = jx * m.in;
+  m.uy = jy * m.in;
+  m.u2 = m.ux * m.ux + m.uy * m.uy;
+  m.X = G1 + m.n * m.u2;
+  m.delta = (ndref + 1.5f * m.X) * m.in;  // 3/2 - J_2 (FD closure)
+  return m;
+}
+
+// Equilibrium and BGK of one cell given J_2, J_4; stores at `off`.
+template <class T, int STAT>
+__device__ __forceinline__ void relax_store_dev(const ProbDev& P, const float g[9], const CellMom& m, float J2,
+                                                float J4, T* __restrict__ fout, int64_t plane, int off) {
+  const float dn = m.dn, X = m.X, ux = m.ux, uy = m.uy, u2 = m.u2;
   // weight changes against the reference (exact algebra, see header comment)
   float dW0, dWs, dWl;
   if (STAT == STAT_FD) {
@@ -177,6 +187,28 @@ __device__ __forceinline__ void collide_store_dev(const ProbDev& P, const float 
   const float w = P.f.omega;
 #pragma unroll
   for (int a = 0; a < 9; ++a) fout[a * plane + off] = Dev<T>::st(fmaf(w, ge[a] - g[a], g[a]));
+}
+
+// Collision of one cell from its pulled deviations g[9]; stores at `off`.
+template <class T, int STAT, bool SURR = false>
+__device__ __forceinline__ void collide_store_dev(const ProbDev& P, const float g[9], T* __restrict__ fout,
+                                                  int64_t plane, int off, const InvLimitsF& L,
+                                                  const MlpParams* W = nullptr, int* fallback = nullptr) {
+  const CellMom m = dev_moments(P, g);
+  float J2, J4;
+  if (STAT == STAT_FD) {
+    J2 = 1.5f - m.delta;
+    if (SURR) {
+      J4 = j4_surrogate_f(m.n, m.delta, L, *W, fallback);
+    } else {
+      float xx;
+      J4 = j4_from_delta_f(m.delta, L, &xx);
+    }
+  } else {
+    J2 = (float)FixedJ<STAT>::j2;
+    J4 = (float)FixedJ<STAT>::j4;
+  }
+  relax_store_dev<T, STAT>(P, g, m, J2, J4, fout, plane, off);
 }
 
 // Pulled deviations of cell (x, y): branch-free gather for interior tiles,
@@ -283,6 +315,150 @@ __global__ void __launch_bounds__(kTileX) stream_collide_surr(const T* __restric
       }
     }
   } while (PERSIST && (tile += (int)gridDim.x) < ntiles);
+}
+
+// The FD step with the learned inversion, its 64 x 64 hidden layer on the
+// tensor cores.  A tile row of 128 cells is one M = 128 MMA operand: every
+// thread computes its cell's first layer (64 SiLU units) and writes it as
+// FP16 into shared memory in the canonical K-major layout; one thread issues
+// four tcgen05.mma (K = 16 each) against W2 (FP16, staged once per CTA from
+// w2h, already in the canonical layout) into an FP32 accumulator of 64 TMEM
+// columns and commits to an mbarrier; each warp then reads its 32 lanes back
+// (tcgen05.ld 32x32b.x64: one row, i.e. one cell, per thread), and the
+// second SiLU, the output layer, the Newton polish and the relaxation run per
+// thread.  A wait that exceeds its bound marks the CTA failed: it counts the
+// event in counters[2], serves the remaining cells with the exact inversion
+// and still frees its TMEM.
+template <class T, int TY, bool PERSIST>
+__global__ void __launch_bounds__(kTileX) stream_collide_surr_tc(const T* __restrict__ fin, T* __restrict__ fout,
+                                                                 const ProbDev* __restrict__ probs, int nprob,
+                                                                 int ntiles, int64_t plane, InvLimitsF L,
+                                                                 unsigned long long* __restrict__ counters,
+                                                                 const __half* __restrict__ w2h, const MlpParams W) {
+  __shared__ __align__(1024) __half sA[kTileX * kH];
+  __shared__ __align__(1024) __half sB[kH * kH];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  const int tid = (int)threadIdx.x, warp = tid >> 5;
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(w2h);
+    uint4* dst = reinterpret_cast<uint4*>(sB);
+    for (int i = tid; i < kH * kH / 8; i += kTileX) dst[i] = src[i];
+  }
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  if (warp == 0) tc::tmem_alloc(&tmem_slot, kH);
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = tc::idesc_f16_f32(kTileX, kH);
+  uint32_t phase = 0;
+  bool failed = false;
+  int tile = (int)blockIdx.x;
+#pragma unroll 1
+  do {
+    const int p = nprob == 1 ? 0 : find_problem(probs, nprob, tile);
+    const ProbDev& P = probs[p];
+    const int lt = tile - (int)P.tile_begin;
+    const int ty = lt / P.tiles_x;
+    const int x0 = (lt - ty * P.tiles_x) * kTileX;
+    const int x = x0 + tid;
+    const int y0 = ty * TY;
+    const int y1 = min(y0 + TY, P.ny);
+    const bool xin = x0 >= 1 && x0 + kTileX <= P.nx - 1;
+    const bool active = x < P.nx;
+#pragma unroll 1
+    for (int y = y0; y < y1; ++y) {
+      float g[9];
+      int off = 0;
+      CellMom m;
+      if (active) {
+        off = gather_dev(fin, plane, P, x, y, xin, g);
+        m = dev_moments(P, g);
+      } else {
+        m.n = 1.0f;
+        m.delta = 0.1f;
+      }
+      const bool use_net = active && !failed && net_cell(m.delta, L);
+      // first layer, written as the M = 128 operand (row tid)
+      {
+        const float i0 = (m.n - kSurNMid) * (1.0f / kSurNHalf);
+        const float i1 = (__logf(m.delta) - kSurLdMid) * (1.0f / kSurLdHalf);
+#pragma unroll
+        for (int kc = 0; kc < kH / 8; ++kc) {
+          __align__(16) __half h[8];
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const int k = 8 * kc + kk;
+            const float z = fmaf(W.p[kOW1 + 2 * k], i0, fmaf(W.p[kOW1 + 2 * k + 1], i1, W.p[kOB1 + k]));
+            h[kk] = __float2half_rn(use_net ? silu_f(z) : 0.0f);
+          }
+          *reinterpret_cast<uint4*>(reinterpret_cast<char*>(sA) + tc::kmajor_off(tid, 8 * kc, kTileX)) =
+              *reinterpret_cast<const uint4*>(h);
+        }
+      }
+      bool ok = false;
+      if (!failed) {
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (tid == 0) {
+          const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+#pragma unroll
+          for (int sidx = 0; sidx < kH / 16; ++sidx) {
+            const uint64_t ad = tc::smem_desc(a0 + (uint32_t)(2 * sidx) * (kTileX / 8) * 128, (kTileX / 8) * 128, 128);
+            const uint64_t bd = tc::smem_desc(b0 + (uint32_t)(2 * sidx) * (kH / 8) * 128, (kH / 8) * 128, 128);
+            tc::mma_f16(tmem, ad, bd, idesc, sidx > 0 ? 1u : 0u);
+          }
+          tc::commit(&mbar);
+        }
+        const bool done = tc::mbar_wait(&mbar, phase, 1 << 22);
+        phase ^= 1u;
+        failed = __syncthreads_or(!done) != 0;
+        if (failed && tid == 0) atomicAdd(&counters[2], 1ull);
+        ok = !failed;
+      }
+      float J4 = 0.0f;
+      int fb = 0;
+      if (ok) {
+        tc::fence_after();
+        float z2[kH];
+        tc::tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16), z2);
+        if (use_net) {
+          float a0 = W.p[kOB3], a1 = W.p[kOB3 + 1];
+#pragma unroll
+          for (int j = 0; j < kH; ++j) {
+            const float h = silu_f(z2[j] + W.p[kOB2 + j]);
+            a0 = fmaf(W.p[kOW3 + j], h, a0);
+            a1 = fmaf(W.p[kOW3 + kH + j], h, a1);
+          }
+          float temp, mu;
+          mlp_outputs_to_state(a0, a1, temp, mu);
+          J4 = j4_polish_f(mu * rcp_a(temp), m.delta, L, &fb);
+        }
+      }
+      if (active) {
+        if (!use_net || !ok) {
+          float xx;
+          J4 = j4_from_delta_f(m.delta, L, &xx);
+          if (use_net) fb = 1;
+        }
+        relax_store_dev<T, STAT_FD>(P, g, m, 1.5f - m.delta, J4, fout, plane, off);
+      }
+      const unsigned nfb = __ballot_sync(0xffffffffu, fb != 0);
+      const unsigned nact = __ballot_sync(0xffffffffu, active);
+      if ((tid & 31) == 0 && nact) {
+        atomicAdd(&counters[0], (unsigned long long)__popc(nfb));
+        atomicAdd(&counters[1], (unsigned long long)__popc(nact));
+      }
+      tc::fence_before();  // this row's TMEM reads before the next row's MMA
+    }
+  } while (PERSIST && (tile += (int)gridDim.x) < ntiles);
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 0) tc::tmem_dealloc(tmem, kH);
 }
 
 }  // namespace lbm

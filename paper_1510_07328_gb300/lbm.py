@@ -97,6 +97,7 @@ def _load():
         "lbm_surrogate_eval": (C.c_int, [V, V, V, C.c_int64, V, V, C.c_int32, V]),
         "lbm_surrogate_load": (C.c_int, [V, V]),
         "lbm_surrogate_stats": (C.c_int, [V, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "lbm_surrogate_engine": (C.c_int, [V, C.c_int32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -110,7 +111,8 @@ EXPORTS = ("lbm_create", "lbm_init_riemann", "lbm_step", "lbm_moments", "lbm_get
            "lbm_set_populations", "lbm_destroy", "lbm_last_error", "lbm_launch_count",
            "lbm_conservation_sums_static", "lbm_set_tiling", "lbm_get_tiling", "lbm_autotune",
            "lbm_surrogate_targets", "lbm_surrogate_loss_grad", "lbm_surrogate_train", "lbm_surrogate_eval",
-           "lbm_surrogate_load", "lbm_surrogate_stats")
+           "lbm_surrogate_load", "lbm_surrogate_stats", "lbm_surrogate_engine")
+LBM_SURROGATE_FP32_PIPE, LBM_SURROGATE_TENSOR_CORES = 0, 1
 NPARAM = 4482
 
 
@@ -295,6 +297,12 @@ def lbm_surrogate_eval(params, n, e):
 def lbm_surrogate_load(ctx, params):
     p, pp = _f32(params)
     _check(LIB.lbm_surrogate_load(ctx, pp), ctx)
+
+
+def lbm_surrogate_engine(ctx, engine: str = "tensor"):
+    """'tensor' (tcgen05 hidden layer, default) or 'fp32' (FP32 pipe)."""
+    _check(LIB.lbm_surrogate_engine(ctx, LBM_SURROGATE_TENSOR_CORES if engine == "tensor" else
+                                    LBM_SURROGATE_FP32_PIPE), ctx)
 
 
 def lbm_surrogate_stats(ctx) -> dict:

@@ -117,17 +117,20 @@ def test_learned_step_parity(L, trained, prec):
 
 def test_learned_inversion_against_exact_path(L, trained):
     """What the network gains over the method without it: fields after 10
-    steps agree with the exact-inversion path to FP32 accuracy; the fallback
-    fraction and the time of both paths are printed (the network costs about
-    4.5 k FMA per cell, the exact inversion a few hundred instructions)."""
+    steps agree with the exact-inversion path to FP32 accuracy, for the hidden
+    layer on the tensor cores and on the FP32 pipe; the fallback fraction and
+    the time of each path are printed (the network costs about 4.5 k MAC per
+    cell, the exact inversion a few hundred instructions)."""
     import torch
 
     p_net, _ = trained
     prob = inputs.random_field(512, 128, 62, tau=0.8, u_max=0.01, n_lo=0.95, n_hi=1.05, t_lo=0.03, t_hi=0.2)
     res = {}
-    for inv in ("exact", "surrogate"):
+    for name, inv, engine in (("exact", "exact", None), ("fp32", "surrogate", "fp32"), ("tensor", "surrogate", "tensor")):
         lat = L.Lattice([prob], prec="f32", inv=inv, surrogate=p_net if inv == "surrogate" else None,
                         n_ref=1.0, t_ref=0.1)
+        if engine:
+            L.lbm_surrogate_engine(lat.ctx, engine)
         lat.init()
         lat.step(2)
         torch.cuda.synchronize()
@@ -136,14 +139,15 @@ def test_learned_inversion_against_exact_path(L, trained):
         lat.step(8)
         e1.record()
         torch.cuda.synchronize()
-        res[inv] = (lat.fields(0), e0.elapsed_time(e1) / 8)
-        if inv == "surrogate":
-            st = L.lbm_surrogate_stats(lat.ctx)
+        st = L.lbm_surrogate_stats(lat.ctx) if engine else None
+        res[name] = (lat.fields(0), e0.elapsed_time(e1) / 8, st)
         lat.close()
-    fa, fb = res["exact"][0], res["surrogate"][0]
-    assert np.abs(fa["n"] - fb["n"]).max() < 1e-5
-    assert np.abs(fa["ux"] - fb["ux"]).max() < 1e-5
-    frac = st["fallbacks"] / max(st["evaluations"], 1)
-    print(f"learned inversion: fallback fraction {frac:.4f}, ms/step exact {res['exact'][1]:.4f}, "
-          f"learned {res['surrogate'][1]:.4f}")
-    assert frac < 0.1
+    fa = res["exact"][0]
+    for name in ("fp32", "tensor"):
+        fb, ms, st = res[name]
+        assert np.abs(fa["n"] - fb["n"]).max() < 1e-5
+        assert np.abs(fa["ux"] - fb["ux"]).max() < 1e-5
+        frac = st["fallbacks"] / max(st["evaluations"], 1)
+        print(f"learned inversion ({name}): fallback fraction {frac:.4f}, ms/step {ms:.4f} "
+              f"(exact {res['exact'][1]:.4f})")
+        assert frac < 0.1
