@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kTileX) stream_collide_surr(const T* __restric
 // thread computes its cell's first layer (64 SiLU units) and writes it as
 // FP16 into shared memory in the canonical K-major layout; one thread issues
 // four tcgen05.mma (K = 16 each) against W2 (FP16, staged once per CTA from
-// w2h, already in the canonical layout) into an FP32 accumulator of 64 TMEM
+// w2h, already in the canonical layout; SiLU by packed FP16 tanh) into an FP32 accumulator of 64 TMEM
 // columns and commits to an mbarrier; each warp then reads its 32 lanes back
 // (tcgen05.ld 32x32b.x64: one row, i.e. one cell, per thread), and the
 // second SiLU, the output layer, the Newton polish and the relaxation run per
@@ -387,12 +387,13 @@ __global__ void __launch_bounds__(kTileX) stream_collide_surr_tc(const T* __rest
         const float i1 = (__logf(m.delta) - kSurLdMid) * (1.0f / kSurLdHalf);
 #pragma unroll
         for (int kc = 0; kc < kH / 8; ++kc) {
-          __align__(16) __half h[8];
+          __align__(16) __half2 h[4];
 #pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {
+          for (int kk = 0; kk < 8; kk += 2) {
             const int k = 8 * kc + kk;
-            const float z = fmaf(W.p[kOW1 + 2 * k], i0, fmaf(W.p[kOW1 + 2 * k + 1], i1, W.p[kOB1 + k]));
-            h[kk] = __float2half_rn(use_net ? silu_f(z) : 0.0f);
+            const float z0 = fmaf(W.p[kOW1 + 2 * k], i0, fmaf(W.p[kOW1 + 2 * k + 1], i1, W.p[kOB1 + k]));
+            const float z1 = fmaf(W.p[kOW1 + 2 * k + 2], i0, fmaf(W.p[kOW1 + 2 * k + 3], i1, W.p[kOB1 + k + 1]));
+            h[kk / 2] = use_net ? tc::silu2_h(z0, z1) : __floats2half2_rn(0.0f, 0.0f);
           }
           *reinterpret_cast<uint4*>(reinterpret_cast<char*>(sA) + tc::kmajor_off(tid, 8 * kc, kTileX)) =
               *reinterpret_cast<const uint4*>(h);
@@ -429,10 +430,10 @@ __global__ void __launch_bounds__(kTileX) stream_collide_surr_tc(const T* __rest
         if (use_net) {
           float a0 = W.p[kOB3], a1 = W.p[kOB3 + 1];
 #pragma unroll
-          for (int j = 0; j < kH; ++j) {
-            const float h = silu_f(z2[j] + W.p[kOB2 + j]);
-            a0 = fmaf(W.p[kOW3 + j], h, a0);
-            a1 = fmaf(W.p[kOW3 + kH + j], h, a1);
+          for (int j = 0; j < kH; j += 2) {
+            const float2 h = __half22float2(tc::silu2_h(z2[j] + W.p[kOB2 + j], z2[j + 1] + W.p[kOB2 + j + 1]));
+            a0 = fmaf(W.p[kOW3 + j], h.x, fmaf(W.p[kOW3 + j + 1], h.y, a0));
+            a1 = fmaf(W.p[kOW3 + kH + j], h.x, fmaf(W.p[kOW3 + kH + j + 1], h.y, a1));
           }
           float temp, mu;
           mlp_outputs_to_state(a0, a1, temp, mu);

@@ -110,5 +110,16 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
   for (int c = 0; c < 64; ++c) v[c] = __uint_as_float(r[c]);
 }
 
+// SiLU of two values in FP16: silu(z) = (z/2)(1 + tanh(z/2)), one packed
+// tanh.approx.f16x2 for both (about 1e-3 relative, the order of the FP16
+// rounding the tensor-core operands carry anyway).
+__device__ __forceinline__ __half2 silu2_h(float z0, float z1) {
+  const __half2 hz = __floats2half2_rn(0.5f * z0, 0.5f * z1);
+  uint32_t t;
+  asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(*reinterpret_cast<const uint32_t*>(&hz)));
+  const __half2 th = *reinterpret_cast<const __half2*>(&t);
+  return __hfma2(hz, th, hz);
+}
+
 }  // namespace tc
 }  // namespace lbm
