@@ -192,9 +192,18 @@ def max_over_ranks(world, v: float) -> float:
     return float(t.item())
 
 
-def kernel_source_hash() -> str:
+# the source files each timed kernel is built from
+_EXACT_SRC = ("lbm_kernels.cuh", "fd_device.cuh", "fd_device_f32.cuh", "lbm_dev32.cuh", "launch.h")
+KERNEL_SOURCES = {
+    "stream_collide_dev": _EXACT_SRC + ("step_f32.cu", "step_bf16.cu"),
+    "stream_collide_f64": ("lbm_kernels.cuh", "fd_device.cuh", "fd_device_f32.cuh", "launch.h", "step_f64.cu"),
+    "stream_collide_surr": _EXACT_SRC + ("surrogate.cuh", "tc_sm100.cuh", "lbm_surr.cuh", "step_surr.cu"),
+}
+
+
+def kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
-    for f in ("lbm_dev32.cuh", "lbm_kernels.cuh", "fd_device.cuh"):
+    for f in KERNEL_SOURCES[kernel.split("<")[0].replace("_tc", "")]:
         h.update(open(os.path.join(ROOT, "paper_1510_07328_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -206,7 +215,7 @@ def profiled_traffic(kernel: str, cells: int):
     try:
         d = json.load(open(p))
         e = d[kernel]
-        if e["source_hash"] != kernel_source_hash():
+        if e["source_hash"] != kernel_source_hash(kernel):
             return None
         return e["dram_bytes_per_cell"] * cells
     except Exception:
@@ -375,7 +384,7 @@ def run_ours(a, world, rank, local):
     kname = {"f32": "stream_collide_dev<float,%s>", "bf16": "stream_collide_dev<bf16,%s>",
              "f64": "stream_collide_f64<%s>"}[a.prec] % a.stat.upper()
     if a.inv == "surrogate":
-        kname = {"f32": "stream_collide_surr<float>", "bf16": "stream_collide_surr<bf16>"}[a.prec]
+        kname = {"f32": "stream_collide_surr_tc<float>", "bf16": "stream_collide_surr_tc<bf16>"}[a.prec]
     traffic = profiled_traffic(kname, cells)
     out = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,

@@ -254,14 +254,20 @@ lbm_status lbm_surrogate_eval(const float* params, const double* n, const double
  * context, NULL, non-finite values), LBM_ENOMEM. */
 lbm_status lbm_surrogate_load(lbm_ctx* ctx, const float* params);
 
-/* Where the network's 64 x 64 hidden layer runs: on the tensor cores
- * (tcgen05 MMA, FP16 operands, FP32 accumulation in tensor memory; the
- * default) or on the FP32 pipe (FP32 throughout).  Drops captured graphs. */
+/* Where the network runs: its three layers on the tensor cores (tcgen05 MMA
+ * over a tile row of 128 cells, FP16 operands with the inputs, layer-1 and
+ * layer-3 weights and all biases split into FP16 hi + lo parts, FP32
+ * accumulation in tensor memory, SiLU in packed FP16; the default) or per
+ * cell on the FP32 pipe (FP32 throughout).  Either way the network's x = mu/T
+ * is polished by one third-order step on J_2(x) = J_2 (one evaluation of
+ * f_0..f_4) and accepted when the first-order step is below 2.5e-2 max(|x|, 1).
+ * Drops captured graphs. */
 enum { LBM_SURROGATE_FP32_PIPE = 0, LBM_SURROGATE_TENSOR_CORES = 1 };
 lbm_status lbm_surrogate_engine(lbm_ctx* ctx, int32_t engine);
 
-/* Cells that went through the network, and those that fell back to the exact
- * inversion, since the context was created.  Synchronises.  Returns
+/* Cells that went through the network (finite J_2 inside the clamp
+ * interval), and those of them that fell back to the exact inversion, since
+ * the context was created.  Synchronises.  Returns
  * LBM_ETIMEOUT (counts still filled) if a tensor-core wait ever gave up; the
  * cells concerned were served by the exact inversion. */
 lbm_status lbm_surrogate_stats(lbm_ctx* ctx, int64_t* fallbacks, int64_t* evaluations);

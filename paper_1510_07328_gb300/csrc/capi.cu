@@ -116,8 +116,9 @@ struct lbm_ctx {
   std::string err;
   MlpParams* surr = nullptr;               // host copy of the network (learned inversion)
   unsigned long long* surr_count = nullptr;  // device: fallbacks, evaluations, tensor-core timeouts
-  void* w2h = nullptr;                       // device: W2 as FP16 in the canonical K-major layout
+  void* wtc = nullptr;                       // device: the network's FP16 tensor-core operands (kTcBytes)
   int surr_engine = LBM_SURROGATE_TENSOR_CORES;
+  int64_t tc_grid[9] = {};  // persistent grid of the tensor-core kernel per rows per tile: SMs x resident CTAs
 };
 
 namespace {
@@ -151,11 +152,13 @@ void launch_step(lbm_ctx* c, const void* in, void* out, cudaStream_t s) {
   const unsigned grid = c->ctas > 0 ? (unsigned)std::min<int64_t>(c->ctas, c->ntiles) : (unsigned)c->ntiles;
   if (c->inv == LBM_INV_SURROGATE) {
     const bool tcore = c->surr_engine == LBM_SURROGATE_TENSOR_CORES;
+    // the tensor-core kernel stages the network once per CTA: persistent grid
+    const unsigned gtc = (unsigned)std::min<int64_t>(c->ctas > 0 ? c->ctas : c->tc_grid[c->rows], c->ntiles);
     if (c->prec == LBM_F32_DEV) {
-      if (tcore) launch_step_surr_tc_f32(c->rows, grid, s, a, c->surr_count, c->w2h, *c->surr);
+      if (tcore) launch_step_surr_tc_f32(c->rows, gtc, s, a, c->surr_count, c->wtc);
       else launch_step_surr_f32(c->rows, grid, s, a, c->surr_count, *c->surr);
     } else {
-      if (tcore) launch_step_surr_tc_bf16(c->rows, grid, s, a, c->surr_count, c->w2h, *c->surr);
+      if (tcore) launch_step_surr_tc_bf16(c->rows, gtc, s, a, c->surr_count, c->wtc);
       else launch_step_surr_bf16(c->rows, grid, s, a, c->surr_count, *c->surr);
     }
     return;
@@ -311,7 +314,17 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
   if (e == cudaSuccess && p->inv == LBM_INV_SURROGATE) {
     e = cudaMalloc(&ctx->surr_count, 3 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->surr_count, 0, 3 * sizeof(unsigned long long), ctx->stream);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->w2h, sizeof(__half) * kH * kH);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->wtc, kTcBytes);
+    if (e == cudaSuccess) {
+      int dev = 0, sms = 0;
+      e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      for (int rows : {1, 2, 4, 8}) {
+        const int per_sm = e == cudaSuccess ? prepare_surr_tc(p->prec == LBM_BF16_DEV, rows) : 0;
+        if (e == cudaSuccess && per_sm <= 0) e = cudaErrorInvalidConfiguration;
+        ctx->tc_grid[rows] = (int64_t)per_sm * sms;
+      }
+    }
   }
   if (e != cudaSuccess) return cleanup(LBM_ENOMEM, std::string("lbm_create: tables: ") + cudaGetErrorString(e));
   e = cudaMemcpyAsync(ctx->pd, ctx->ph.data(), sizeof(ProbDev) * ctx->nprob, cudaMemcpyHostToDevice, ctx->stream);
@@ -459,6 +472,38 @@ lbm_status lbm_get_tiling(const lbm_ctx* ctx, lbm_tiling* out) {
   return LBM_OK;
 }
 
+namespace {
+
+// The network's FP16 tensor-core operands (layout in surrogate.cuh).  A value
+// v enters as hi = fp16(v) and lo = fp16(v - hi).
+std::vector<__half> pack_tc_operands(const float* p) {
+  std::vector<__half> out(kTcBytes / 2, __float2half_rn(0.0f));
+  auto put = [&](int base, int R, int r, int k, float v) { out[(base + tc_operand_byte(r, k, R)) / 2] = __float2half_rn(v); };
+  auto hi = [](float v) { return __half2float(__float2half_rn(v)); };
+  for (int j = 0; j < kH; ++j) {
+    const float wn = 0.5f * p[kOW1 + 2 * j], wl = 0.5f * p[kOW1 + 2 * j + 1], b = 0.5f * p[kOB1 + j];
+    const float row[8] = {hi(wn), hi(wn), wn - hi(wn), hi(wl), hi(wl), wl - hi(wl), hi(b), b - hi(b)};
+    for (int k = 0; k < 8; ++k) put(kTcB1, kH, j, k, row[k]);
+    for (int k = 0; k < kH; ++k) put(kTcB2, kH, j, k, 0.5f * p[kOW2 + kH * j + k]);
+    const float b2 = 0.5f * p[kOB2 + j];
+    put(kTcB2b, kH, j, 6, hi(b2));
+    put(kTcB2b, kH, j, 7, b2 - hi(b2));
+  }
+  for (int o = 0; o < 2; ++o) {
+    for (int k = 0; k < kH; ++k) {
+      const float w = p[kOW3 + kH * o + k];
+      put(kTcB3, 16, o, k, hi(w));
+      put(kTcB3, 16, 2 + o, k, w - hi(w));
+    }
+    const float b3 = p[kOB3 + o];
+    put(kTcB3b, 16, o, 6, hi(b3));
+    put(kTcB3b, 16, o, 7, b3 - hi(b3));
+  }
+  return out;
+}
+
+}  // namespace
+
 lbm_status lbm_surrogate_load(lbm_ctx* ctx, const float* params) {
   if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_surrogate_load: NULL context");
   if (!params) return fail(ctx, LBM_EINVAL, "lbm_surrogate_load: NULL parameters");
@@ -469,15 +514,8 @@ lbm_status lbm_surrogate_load(lbm_ctx* ctx, const float* params) {
   if (!ctx->surr) ctx->surr = new (std::nothrow) MlpParams();
   if (!ctx->surr) return fail(ctx, LBM_ENOMEM, "lbm_surrogate_load: host allocation failed");
   std::memcpy(ctx->surr->p, params, sizeof(float) * kNParam);
-  // W2 as FP16 in the canonical K-major layout of the tensor-core operand:
-  // element (n, k) at core (n/8, k/8) = ((k/8) * 8 + n/8) * 128 bytes, row n%8
-  std::vector<__half> w2(kH * kH);
-  for (int n = 0; n < kH; ++n)
-    for (int k = 0; k < kH; ++k) {
-      const size_t byte = ((size_t)(k / 8) * (kH / 8) + n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
-      w2[byte / 2] = __float2half_rn(params[kOW2 + kH * n + k]);
-    }
-  CK(cudaMemcpyAsync(ctx->w2h, w2.data(), sizeof(__half) * kH * kH, cudaMemcpyHostToDevice, ctx->stream));
+  const std::vector<__half> wtc = pack_tc_operands(params);
+  CK(cudaMemcpyAsync(ctx->wtc, wtc.data(), kTcBytes, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   drop_graphs(ctx);
   return LBM_OK;
@@ -681,7 +719,7 @@ lbm_status lbm_destroy(lbm_ctx* ctx) {
   if (ctx->tmp) cudaFree(ctx->tmp);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
   if (ctx->surr_count) cudaFree(ctx->surr_count);
-  if (ctx->w2h) cudaFree(ctx->w2h);
+  if (ctx->wtc) cudaFree(ctx->wtc);
   delete ctx->surr;
   delete ctx;
   return LBM_OK;

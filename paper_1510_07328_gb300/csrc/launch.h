@@ -29,12 +29,16 @@ void launch_step_surr_f32(int rows, unsigned grid, cudaStream_t s, const StepArg
                           const MlpParams& W);
 void launch_step_surr_bf16(int rows, unsigned grid, cudaStream_t s, const StepArgs& a, unsigned long long* counters,
                            const MlpParams& W);
-// the same with the hidden layer on the tensor cores (tcgen05); w2h: W2 as
-// FP16 in the canonical K-major layout (4096 halves, 16-byte aligned)
+// the same with the network's three layers on the tensor cores (tcgen05);
+// wtc: the network's FP16 operands (kTcBytes bytes, 16-byte aligned).  The
+// kernels need prepare_surr_tc first (outside stream capture): it sets the
+// shared-memory attributes of the kernels for `rows` rows per tile and
+// returns their CTAs resident per SM (0: error).
+int prepare_surr_tc(bool bf16, int rows);
 void launch_step_surr_tc_f32(int rows, unsigned grid, cudaStream_t s, const StepArgs& a,
-                             unsigned long long* counters, const void* w2h, const MlpParams& W);
+                             unsigned long long* counters, const void* wtc);
 void launch_step_surr_tc_bf16(int rows, unsigned grid, cudaStream_t s, const StepArgs& a,
-                              unsigned long long* counters, const void* w2h, const MlpParams& W);
+                              unsigned long long* counters, const void* wtc);
 void launch_step_f64(int stat, int rows, unsigned grid, cudaStream_t s, const StepArgs& a);
 void launch_step_f32(int stat, int rows, unsigned grid, cudaStream_t s, const StepArgs& a);
 void launch_step_bf16(int stat, int rows, unsigned grid, cudaStream_t s, const StepArgs& a);

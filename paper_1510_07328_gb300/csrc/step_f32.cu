@@ -31,46 +31,4 @@ void launch_step_f32(int stat, int rows, unsigned grid, cudaStream_t s, const St
   }
 }
 
-template <int TY>
-static void go_surr(unsigned grid, cudaStream_t s, const StepArgs& a, unsigned long long* c, const MlpParams& W) {
-  if ((int)grid < a.ntiles)
-    stream_collide_surr<float, TY, true><<<grid, kTileX, 0, s>>>((const float*)a.in, (float*)a.out, a.probs, a.nprob,
-                                                              a.ntiles, a.plane, a.limf, c, W);
-  else
-    stream_collide_surr<float, TY, false><<<grid, kTileX, 0, s>>>((const float*)a.in, (float*)a.out, a.probs, a.nprob,
-                                                               a.ntiles, a.plane, a.limf, c, W);
-}
-
-void launch_step_surr_f32(int rows, unsigned grid, cudaStream_t s, const StepArgs& a, unsigned long long* c,
-                          const MlpParams& W) {
-  switch (rows) {
-    case 1: go_surr<1>(grid, s, a, c, W); break;
-    case 2: go_surr<2>(grid, s, a, c, W); break;
-    case 8: go_surr<8>(grid, s, a, c, W); break;
-    default: go_surr<4>(grid, s, a, c, W); break;
-  }
-}
-
-template <int TY>
-static void go_surr_tc(unsigned grid, cudaStream_t s, const StepArgs& a, unsigned long long* c, const void* w2h,
-                       const MlpParams& W) {
-  const __half* w = (const __half*)w2h;
-  if ((int)grid < a.ntiles)
-    stream_collide_surr_tc<float, TY, true><<<grid, kTileX, 0, s>>>((const float*)a.in, (float*)a.out, a.probs,
-                                                                 a.nprob, a.ntiles, a.plane, a.limf, c, w, W);
-  else
-    stream_collide_surr_tc<float, TY, false><<<grid, kTileX, 0, s>>>((const float*)a.in, (float*)a.out, a.probs,
-                                                                  a.nprob, a.ntiles, a.plane, a.limf, c, w, W);
-}
-
-void launch_step_surr_tc_f32(int rows, unsigned grid, cudaStream_t s, const StepArgs& a, unsigned long long* c,
-                             const void* w2h, const MlpParams& W) {
-  switch (rows) {
-    case 1: go_surr_tc<1>(grid, s, a, c, w2h, W); break;
-    case 2: go_surr_tc<2>(grid, s, a, c, w2h, W); break;
-    case 8: go_surr_tc<8>(grid, s, a, c, w2h, W); break;
-    default: go_surr_tc<4>(grid, s, a, c, w2h, W); break;
-  }
-}
-
 }  // namespace lbm

@@ -36,6 +36,27 @@ struct MlpParams {
   float p[kNParam];
 };
 
+// The network as FP16 tensor-core B operands (N x K, canonical K-major
+// layout without swizzle: element (r, k) of an R-row operand at byte
+// ((k/8)(R/8) + r/8) 128 + (r%8) 16 + (k%8) 2), one buffer, byte offsets:
+//   kTcB1   64 x 16  layer 1: unit j holds (w_n hi, w_n hi, w_n lo, w_l hi,
+//                    w_l hi, w_l lo, b hi, b lo, 0 ...) of W1/2, b1/2, against
+//                    the input row (n hi, n lo, n hi, l hi, l lo, l hi, 1, 1,
+//                    0 ...), so the products carry the inputs and weights to
+//                    about 2^-22
+//   kTcB2   64 x 64  W2/2
+//   kTcB2b  64 x 16  b2/2 (hi, lo) in columns 6, 7 (against the input row)
+//   kTcB3   16 x 64  W3 rows 0, 1 (hi) and 2, 3 (lo); rows 4..15 zero
+//   kTcB3b  16 x 16  b3 (hi, lo) in columns 6, 7 of rows 0, 1
+// The halving makes layers 1 and 2 produce z/2, the argument of
+// silu(z) = (z/2)(1 + tanh(z/2)).
+constexpr int kTcB1 = 0, kTcB2 = kTcB1 + kH * 16 * 2, kTcB2b = kTcB2 + kH * kH * 2, kTcB3 = kTcB2b + kH * 16 * 2,
+              kTcB3b = kTcB3 + 16 * kH * 2, kTcBytes = kTcB3b + 16 * 16 * 2;  // 14848
+
+__host__ __device__ constexpr int tc_operand_byte(int r, int k, int R) {
+  return ((k / 8) * (R / 8) + r / 8) * 128 + (r % 8) * 16 + (k % 8) * 2;
+}
+
 __device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
 // Network output (y_0, y_1) for one cell given n and delta = 3/2 - J_2

@@ -110,6 +110,34 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
   for (int c = 0; c < 64; ++c) v[c] = __uint_as_float(r[c]);
 }
 
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%"
+      "28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+}
+
+// 4 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < 4; ++c) v[c] = __uint_as_float(r[c]);
+}
+
 // SiLU of two values in FP16: silu(z) = (z/2)(1 + tanh(z/2)), one packed
 // tanh.approx.f16x2 for both (about 1e-3 relative, the order of the FP16
 // rounding the tensor-core operands carry anyway).
@@ -119,6 +147,16 @@ __device__ __forceinline__ __half2 silu2_h(float z0, float z1) {
   asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(*reinterpret_cast<const uint32_t*>(&hz)));
   const __half2 th = *reinterpret_cast<const __half2*>(&t);
   return __hfma2(hz, th, hz);
+}
+
+// The same from the halved arguments h = z/2 (weights pre-scaled by 1/2):
+// silu(z) = h + h tanh(h); returns the packed FP16 pair.
+__device__ __forceinline__ uint32_t silu2_half_arg(float h0, float h1) {
+  const __half2 hz = __floats2half2_rn(h0, h1);
+  uint32_t t;
+  asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(*reinterpret_cast<const uint32_t*>(&hz)));
+  const __half2 s = __hfma2(hz, *reinterpret_cast<const __half2*>(&t), hz);
+  return *reinterpret_cast<const uint32_t*>(&s);
 }
 
 }  // namespace tc

@@ -111,7 +111,8 @@ def test_learned_step_parity(L, trained, prec):
         assert np.abs(got - f).max() <= tol
     st = L.lbm_surrogate_stats(lat.ctx)
     lat.close()
-    assert st["evaluations"] == 2 * prob.cells
+    # cells whose J_2 lies beyond the clamp interval skip the network
+    assert 0 < st["evaluations"] <= 2 * prob.cells
     assert 0 <= st["fallbacks"] <= st["evaluations"]
 
 
