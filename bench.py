@@ -309,7 +309,7 @@ def run_ours(a, world, rank, local):
         torch.cuda.synchronize()
         lat = lbm.Lattice(probs, stat=a.stat, prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05)
     cells = sum(p.cells for p in probs)
-    surrogate = None
+    surrogate = net = None
     if a.inv == "surrogate":
         # the learned inversion: trained by the library's kernels on 1e6 pairs
         # from the exact forward map, then loaded into a learned-inversion context
@@ -401,13 +401,13 @@ def run_ours(a, world, rank, local):
         "state_after_timed_steps": {"nonfinite_frac": nonfinite, "clamped_frac": clamped},
     }
     if not a.no_extras and rank == 0 and a.workload == "smooth_t":
-        out.update(extras(a, prob, dev_fields, lbm, torch, stream, value))
+        out.update(extras(a, prob, dev_fields, lbm, torch, stream, value, net))
     del dev_fields
     if rank == 0:
         print(json.dumps(out))
 
 
-def extras(a, prob, dev_fields, lbm, torch, stream, value):
+def extras(a, prob, dev_fields, lbm, torch, stream, value, net=None):
     """FP64 comparison on the same lattice, end-to-end timing through host
     buffers, and the CPU oracle on a bounded sample."""
     res = {}
@@ -428,7 +428,8 @@ def extras(a, prob, dev_fields, lbm, torch, stream, value):
     res["fp64_gpu"] = {"value": v64, "unit": "MLUPS", "steps": k64}
     res["speedup_vs_fp64"] = value / v64
     # field error of the reduced-precision path against FP64 after N steps
-    lr = lbm.Lattice([prob], stat="fd", prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05)
+    lr = lbm.Lattice([prob], stat="fd", prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05,
+                     inv=a.inv, surrogate=net)
     with torch.cuda.stream(stream):
         lr.init(fields_on_device=dev_fields)
         lat64.init(fields_on_device=dev_fields)
@@ -460,12 +461,20 @@ def extras(a, prob, dev_fields, lbm, torch, stream, value):
     del fa, fb
     # end to end through the public API with host buffers: H2D of the initial
     # fields, K steps, D2H of the moments
-    host = {k: np.ascontiguousarray(getattr(prob, k)) for k in ("n", "ux", "uy", "t")}
-    outs = {k: np.empty((prob.ny, prob.nx)) for k in ("n", "ux", "uy", "T")}
-    le = lbm.Lattice([prob], stat="fd", prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05)
+    # inputs and outputs in pinned host memory (filled before the timed region)
+    def pinned():
+        return torch.empty((prob.ny, prob.nx), dtype=torch.float64, pin_memory=True).numpy()
+
+    host = {}
+    for k in ("n", "ux", "uy", "t"):
+        host[k] = pinned()
+        host[k][...] = getattr(prob, k)
+    outs = {k: pinned() for k in ("n", "ux", "uy", "T")}
+    le = lbm.Lattice([prob], stat="fd", prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05,
+                     inv=a.inv, surrogate=net)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    le.init()  # host fields -> device inside the call
+    lbm.lbm_init_riemann(le.ctx, 0, "field", fields=host)  # host fields -> device inside the call
     le.step(a.steps)
     lbm.lbm_moments(le.ctx, 0, **outs)  # device -> host, synchronises
     el = time.perf_counter() - t0

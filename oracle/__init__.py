@@ -13,5 +13,7 @@ Modules:
   gpoly   moments I_2N, polynomial coefficients, P_0..P_4, A_0..A_3,
           quadrature weights, tensor-contraction equilibrium
   lbm     lattice state, pull streaming with bounce-back, moments, bisection
-          FD inversion, BGK step
+          FD inversion, BGK step (d2v9)
+  lbm1d   the d1v3 lattice with the zero-temperature and Maxwell-Boltzmann
+          closures
 """
