@@ -48,8 +48,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="f32", choices=["f32", "bf16", "f64"])
     ap.add_argument("--L", type=int, default=4096)
-    ap.add_argument("--workload", default="smooth_t", choices=["smooth_t", "batched"],
-                    help="smooth_t: one 4096^2 lattice; batched: 256 uneven quasi-1D Riemann problems")
+    ap.add_argument("--workload", default="smooth_t", choices=["smooth_t", "batched", "d1v3"],
+                    help="smooth_t: one 4096^2 lattice; batched: 256 uneven quasi-1D Riemann problems; "
+                         "d1v3: the zero-temperature Riemann run of the paper's Fig. 1 on d1v3, scaled to --cells1d")
+    ap.add_argument("--cells1d", type=int, default=1 << 25, help="lattice length of the d1v3 workload")
     ap.add_argument("--autotune", action="store_true", help="autotune the tiling before timing (always on for batched)")
     ap.add_argument("--inv", default="exact", choices=["exact", "surrogate"],
                     help="per-cell FD inversion: exact, or the learned network (trained first, on 1e6 pairs)")
@@ -63,6 +65,20 @@ def parse():
 
 
 def workload_config(a, world, probs=None, tiling=None):
+    if a.workload == "d1v3":
+        return {
+            "workload": f"d1v3_riemann_{a.cells1d}",
+            "lattice": [a.cells1d],
+            "cells": a.cells1d,
+            "stencil": "d1v3 K=3 generalized-polynomial LBGK, " + {"mb": "Maxwell-Boltzmann limit (J = 1)"}.get(
+                a.stat, "theta = 0 closure (J_2 = 5/3)"),
+            "storage": {"f32": "FP32 deviations g = f - W_ref", "bf16": "BF16 deviations", "f64": "FP64 f"}[a.prec],
+            "initial_state": "n = 1.0 for L/4 < x < 3L/4, 0.85 elsewhere, u = 0 (Fig. 1 scaled)",
+            "tau": 0.58,
+            "boundaries": "periodic",
+            "l2": f"inputs larger than L2 ({2 * 3 * a.cells1d * BYTES_PER_ELEM[a.prec] / 1e9:.2f} GB population buffers)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        }
     if a.workload == "batched":
         cells = sum(p.cells for p in probs)
         return {
@@ -198,6 +214,8 @@ KERNEL_SOURCES = {
     "stream_collide_dev": _EXACT_SRC + ("step_f32.cu", "step_bf16.cu"),
     "stream_collide_f64": ("lbm_kernels.cuh", "fd_device.cuh", "fd_device_f32.cuh", "launch.h", "step_f64.cu"),
     "stream_collide_surr": _EXACT_SRC + ("surrogate.cuh", "tc_sm100.cuh", "lbm_surr.cuh", "step_surr.cu"),
+    "stream_collide_d1": ("lbm_kernels.cuh", "fd_device.cuh", "fd_device_f32.cuh", "launch.h", "lbm_d1.cuh",
+                          "step_d1.cu"),
 }
 
 
@@ -301,6 +319,19 @@ def run_ours(a, world, rank, local):
         prob = None
         dev_fields = None
         lat = lbm.Lattice(probs, stat=a.stat, prec=a.prec, stream=stream.cuda_stream, n_ref=1.2, t_ref=0.05)
+    elif a.workload == "d1v3":
+        if a.stat == "fd":
+            a.stat = "t0"  # d1v3 has no finite-temperature closure
+        n1 = a.cells1d
+        xs = np.arange(n1)
+        n = np.where((xs > n1 / 4) & (xs < 3 * n1 / 4), 1.0, 0.85)[None, :]
+        z = np.zeros((1, n1))
+        prob = inputs.Problem(n1, 1, 0.58, "periodic", "periodic", n, z, z.copy(), z.copy(),
+                              name=f"d1v3_riemann_{n1}", kind="field")
+        probs = [prob]
+        dev_fields = {k: torch.from_numpy(getattr(prob, k)).cuda() for k in ("n", "ux", "uy", "t")}
+        torch.cuda.synchronize()
+        lat = lbm.Lattice(probs, stat=a.stat, prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05, dim=1)
     else:
         prob = inputs.smooth_t(a.L, tau=a.tau)
         probs = [prob]
@@ -378,13 +409,16 @@ def run_ours(a, world, rank, local):
 
     value = world * cells * a.steps / (ms_max / 1e3) / 1e6
     per_launch_s = ms / 1e3 / a.steps
-    bytes_per_cell = 18 * BYTES_PER_ELEM[a.prec]
+    bytes_per_cell = (6 if a.workload == "d1v3" else 18) * BYTES_PER_ELEM[a.prec]
     achieved = bytes_per_cell * cells / per_launch_s / 1e9
     peak, peak_kind = peaks()
     kname = {"f32": "stream_collide_dev<float,%s>", "bf16": "stream_collide_dev<bf16,%s>",
              "f64": "stream_collide_f64<%s>"}[a.prec] % a.stat.upper()
     if a.inv == "surrogate":
         kname = {"f32": "stream_collide_surr_tc<float>", "bf16": "stream_collide_surr_tc<bf16>"}[a.prec]
+    if a.workload == "d1v3":
+        kname = "stream_collide_d1<%s,%s>" % ({"f32": "float", "bf16": "bf16", "f64": "double"}[a.prec],
+                                              a.stat.upper())
     traffic = profiled_traffic(kname, cells)
     out = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,

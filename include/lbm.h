@@ -15,11 +15,16 @@
  * polynomials in D dimensions"), evaluates J_4 = f_3^2/(f_2 f_4), builds f_eq
  * and relaxes.
  *
+ * The d1v3 lattice (D = 1, velocities 0, +1, -1, weights W_0 = n (1 - J_2/3),
+ * W_+-1 = n J_2/6) runs the same calls with the theta = 0 or Maxwell-Boltzmann
+ * closure (lbm_params.dim = 1).
+ *
  * Conventions shared by every call:
- *  - Velocity order a = 0..8: rest; (1,0), (0,1), (-1,0), (0,-1);
- *    (1,1), (-1,1), (-1,-1), (1,-1).
+ *  - Velocity order a = 0..8 on d2v9: rest; (1,0), (0,1), (-1,0), (0,-1);
+ *    (1,1), (-1,1), (-1,-1), (1,-1).  On d1v3, a = 0..2: rest, +1, -1.
  *  - Arrays of per-cell values are row-major [ny][nx] (x fastest), one array
- *    per problem; populations are [9][ny][nx].
+ *    per problem; populations are [Q][ny][nx] with Q = 9 (d2v9) or 3 (d1v3,
+ *    ny = 1).
  *  - All calls are asynchronous on the context's CUDA stream unless stated;
  *    a call that writes host memory synchronises that stream before it returns.
  *  - Every call returns an lbm_status; nothing aborts or throws.  On failure
@@ -78,7 +83,8 @@ typedef struct {
 } lbm_problem;
 
 typedef struct {
-  int32_t dim;       /* 2 (d2v9); other values -> LBM_EUNSUPPORTED */
+  int32_t dim;       /* 2 (d2v9) or 1 (d1v3: every problem ny = 1, stat FD_T0 or MB,
+                        exact inversion); other values -> LBM_EUNSUPPORTED */
   int32_t order;     /* 3 (K = 3 expansion); other values -> LBM_EUNSUPPORTED */
   int32_t stat;      /* lbm_stat */
   int32_t prec;      /* lbm_prec */
@@ -92,8 +98,10 @@ typedef struct {
  * cudaStream_t; NULL = legacy default stream).  Populations start at zero;
  * call lbm_init_riemann for every problem before stepping.
  * Errors: LBM_EINVAL (p or out NULL, nx or ny < 1, tau <= 0.5, bad enum,
- * reference state out of range), LBM_EUNSUPPORTED (dim != 2, order != 3),
- * LBM_ENOMEM, LBM_ECUDA. */
+ * reference state out of range, d1v3 problem with ny != 1), LBM_EUNSUPPORTED
+ * (dim not 1 or 2, order != 3, d1v3 with LBM_STAT_FD: with three velocities
+ * n, j and E fix every population, so no finite-temperature collision
+ * exists; the learned inversion on d1v3), LBM_ENOMEM, LBM_ECUDA. */
 lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out);
 
 /* Initial state of one problem (the Riemann problems of Sect. "Numerical
@@ -104,7 +112,9 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out);
  *  FIELD:    per-cell arrays n, ux, uy, t of nx*ny doubles each, host or
  *            device memory per field_on_device; read during the call only.
  * t is T/T_F (T_F the theta = 0 chemical potential at the cell's density);
- * it must lie in [1e-3, 10] for LBM_STAT_FD and is ignored otherwise. */
+ * it must lie in [1e-3, 10] for LBM_STAT_FD and is ignored otherwise.  On
+ * d1v3 QUADRANT is invalid and uy is ignored (FIELD still takes all four
+ * arrays). */
 typedef enum { LBM_INIT_HALF = 0, LBM_INIT_QUADRANT = 1, LBM_INIT_FIELD = 2 } lbm_init_kind;
 typedef struct { double n, ux, uy, t; } lbm_state;
 typedef struct {
@@ -120,7 +130,7 @@ typedef struct {
 
 /* Errors: LBM_EINVAL (problem index, kind, NULL field, n <= 0 or t out of
  * range in a region state; per-cell field values are not checked on the
- * host), LBM_ENOMEM, LBM_ECUDA. */
+ * host; QUADRANT on d1v3), LBM_ENOMEM, LBM_ECUDA. */
 lbm_status lbm_init_riemann(lbm_ctx* ctx, int32_t problem, const lbm_riemann_desc* d);
 
 /* Advance every problem by nsteps LBGK steps (pull stream + collide, one
@@ -166,14 +176,16 @@ typedef struct {
  * array of nx*ny doubles (any pointer may be NULL to skip that field):
  *  n; u_0 = (ux, uy) in lattice units; T = theta and mu in the paper's
  *  dimensionless units (m = k_B = hbar = 1); t = T/T_F.  For LBM_STAT_FD_T0,
- *  T = t = 0 and mu = T_F = n/(2 pi); for LBM_STAT_MB, T, mu, t are NaN.
+ *  T = t = 0 and mu = T_F, the theta = 0 chemical potential at density n
+ *  (n/(2 pi) on d2v9, n^2/8 on d1v3); for LBM_STAT_MB, T, mu, t are NaN.
+ *  On d1v3 uy is 0 and diag.sum_E = sum of f e^2.
  * out_on_device != 0: the pointers are device memory and the call is
  * asynchronous; otherwise host memory and the call synchronises.  diag may be
  * NULL; if not, the call synchronises and fills it (host memory). */
 lbm_status lbm_moments(lbm_ctx* ctx, int32_t problem, double* n, double* ux, double* uy,
                        double* T, double* mu, double* t, int32_t out_on_device, lbm_diag* diag);
 
-/* Checkpoint / resume: copy the populations f_a (FP64, [9][ny][nx]) of one
+/* Checkpoint / resume: copy the populations f_a (FP64, [Q][ny][nx]) of one
  * problem out of or into the library.  Storage of reduced precision converts
  * (f = W^ref + g on the way out, g = f - W^ref rounded on the way in).
  * on_device selects device or host memory for f; host copies synchronise. */

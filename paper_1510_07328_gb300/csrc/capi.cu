@@ -36,10 +36,24 @@ static __global__ void setup_kernel(InvLimits* out) {
 
 // Deviation reference of each problem: J_2,ref from t_ref (or the closure's
 // constant), W^ref = w_a(J_2,ref) n_ref and n_ref (3/2 - J_2,ref).
-static __global__ void ref_kernel(ProbDev* probs, int nprob, int stat) {
+static __global__ void ref_kernel(ProbDev* probs, int nprob, int stat, int dim) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nprob) return;
   ProbDev& P = probs[p];
+  if (dim == 1) {  // d1v3: W_0 = n (1 - J_2/3), W_+-1 = n J_2/6
+    const double J2 = stat == STAT_T0 ? 5.0 / 3.0 : 1.0, n = P.n_ref;
+    P.j2_ref = J2;
+    P.ndelta_ref = 0.0;
+    P.wref[0] = n * (1.0 - J2 / 3.0);
+    P.wref[1] = P.wref[2] = n * J2 / 6.0;
+    for (int a = 3; a < 9; ++a) P.wref[a] = 0.0;
+    P.f.omega = (float)P.omega;
+    P.f.n_ref = (float)n;
+    P.f.ndelta_ref = 0.0f;
+    P.f.wref[0] = (float)P.wref[0];
+    P.f.wref[1] = P.f.wref[2] = (float)P.wref[1];
+    return;
+  }
   double J2, J4;
   if (stat == STAT_FD) {
     if (P.n_ref > 0.0) closure_from_t<STAT_FD>(P.t_ref, J2, J4); else J2 = 1.5;
@@ -97,6 +111,7 @@ struct lbm_ctx {
   std::vector<ProbDev> ph;  // host copy of the device table
   ProbDev* pd = nullptr;
   int64_t plane = 0, ntiles = 0;
+  int dim = 2, q = 9;        // lattice: d2v9 or d1v3
   int rows = kTileYDefault;  // rows per tile
   int ctas = 0;              // 0: one CTA per tile; else a persistent grid of this many CTAs
   void* buf[2] = {nullptr, nullptr};
@@ -150,6 +165,10 @@ unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 void launch_step(lbm_ctx* c, const void* in, void* out, cudaStream_t s) {
   StepArgs a{in, out, c->pd, c->nprob, (int)c->ntiles, c->plane, c->lim, c->limf};
   const unsigned grid = c->ctas > 0 ? (unsigned)std::min<int64_t>(c->ctas, c->ntiles) : (unsigned)c->ntiles;
+  if (c->dim == 1) {
+    launch_step_d1(c->prec, c->stat, grid, s, a);
+    return;
+  }
   if (c->inv == LBM_INV_SURROGATE) {
     const bool tcore = c->surr_engine == LBM_SURROGATE_TENSOR_CORES;
     // the tensor-core kernel stages the network once per CTA: persistent grid
@@ -242,18 +261,24 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
   lbm_ctx* ctx = nullptr;
   if (!p || !out) return fail(nullptr, LBM_EINVAL, "lbm_create: NULL argument");
   *out = nullptr;
-  if (p->dim != 2) return fail(nullptr, LBM_EUNSUPPORTED, "lbm_create: only dim = 2 (d2v9) is implemented");
+  if (p->dim != 1 && p->dim != 2)
+    return fail(nullptr, LBM_EUNSUPPORTED, "lbm_create: dim must be 1 (d1v3) or 2 (d2v9)");
+  if (p->dim == 1 && p->stat == LBM_STAT_FD)
+    return fail(nullptr, LBM_EUNSUPPORTED,
+                "lbm_create: d1v3 has no finite-temperature closure (n, j and E fix its three populations); "
+                "use LBM_STAT_FD_T0 or LBM_STAT_MB");
   if (p->order != 3) return fail(nullptr, LBM_EUNSUPPORTED, "lbm_create: only order K = 3 is implemented");
   if (p->stat < 0 || p->stat > 2) return fail(nullptr, LBM_EINVAL, "lbm_create: bad stat");
   if (p->prec < 0 || p->prec > 2) return fail(nullptr, LBM_EINVAL, "lbm_create: bad prec");
   if (p->inv != LBM_INV_EXACT && p->inv != LBM_INV_SURROGATE) return fail(nullptr, LBM_EINVAL, "lbm_create: bad inv");
-  if (p->inv == LBM_INV_SURROGATE && (p->prec == LBM_F64 || p->stat != LBM_STAT_FD))
+  if (p->inv == LBM_INV_SURROGATE && (p->prec == LBM_F64 || p->stat != LBM_STAT_FD || p->dim != 2))
     return fail(nullptr, LBM_EUNSUPPORTED,
                 "lbm_create: the learned inversion needs LBM_STAT_FD with FP32 or BF16 deviation storage");
   if (p->nproblems < 1 || !p->problems) return fail(nullptr, LBM_EINVAL, "lbm_create: no problems");
   for (int i = 0; i < p->nproblems; ++i) {
     const lbm_problem& q = p->problems[i];
     if (q.nx < 1 || q.ny < 1) return fail(nullptr, LBM_EINVAL, "lbm_create: nx, ny must be >= 1");
+    if (p->dim == 1 && q.ny != 1) return fail(nullptr, LBM_EINVAL, "lbm_create: d1v3 problems need ny = 1");
     if ((int64_t)q.nx * q.ny > ((int64_t)1 << 40)) return fail(nullptr, LBM_EINVAL, "lbm_create: problem too large");
     if (!(q.tau > 0.5) || !std::isfinite(q.tau)) return fail(nullptr, LBM_EINVAL, "lbm_create: tau must be > 1/2");
     if ((q.bc_x != 0 && q.bc_x != 1) || (q.bc_y != 0 && q.bc_y != 1))
@@ -268,6 +293,8 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
   if (!ctx) return fail(nullptr, LBM_ENOMEM, "lbm_create: host allocation failed");
   ctx->stat = p->stat;
   ctx->prec = p->prec;
+  ctx->dim = p->dim;
+  ctx->q = p->dim == 1 ? 3 : 9;
   ctx->inv = p->inv;
   ctx->nprob = p->nproblems;
   ctx->probs.assign(p->problems, p->problems + p->nproblems);
@@ -301,7 +328,7 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
     lbm_destroy(ctx);
     return fail(nullptr, s, m);
   };
-  const size_t bytes = (size_t)ctx->plane * 9 * elem_size(ctx->prec);
+  const size_t bytes = (size_t)ctx->plane * ctx->q * elem_size(ctx->prec);
   for (int b = 0; b < 2; ++b) {
     cudaError_t e = cudaMalloc(&ctx->buf[b], bytes);
     if (e != cudaSuccess) return cleanup(LBM_ENOMEM, std::string("lbm_create: population buffers: ") + cudaGetErrorString(e));
@@ -330,7 +357,7 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
   e = cudaMemcpyAsync(ctx->pd, ctx->ph.data(), sizeof(ProbDev) * ctx->nprob, cudaMemcpyHostToDevice, ctx->stream);
   if (e != cudaSuccess) return cleanup(LBM_ECUDA, std::string("lbm_create: upload: ") + cudaGetErrorString(e));
   setup_kernel<<<1, 1, 0, ctx->stream>>>(ctx->lim_d);
-  ref_kernel<<<blocks_for(ctx->nprob, 64), 64, 0, ctx->stream>>>(ctx->pd, ctx->nprob, ctx->stat);
+  ref_kernel<<<blocks_for(ctx->nprob, 64), 64, 0, ctx->stream>>>(ctx->pd, ctx->nprob, ctx->stat, ctx->dim);
   ctx->launches += 2;
   e = cudaMemcpyAsync(&ctx->lim, ctx->lim_d, sizeof(InvLimits), cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->ph.data(), ctx->pd, sizeof(ProbDev) * ctx->nprob, cudaMemcpyDeviceToHost, ctx->stream);
@@ -353,6 +380,8 @@ lbm_status lbm_init_riemann(lbm_ctx* ctx, int32_t problem, const lbm_riemann_des
   k.kind = d->kind;
   k.x0 = d->x0;
   k.y0 = d->y0;
+  if (ctx->dim == 1 && d->kind == LBM_INIT_QUADRANT)
+    return fail(ctx, LBM_EINVAL, "lbm_init_riemann: QUADRANT needs a two-dimensional lattice");
   if (d->kind == LBM_INIT_HALF || d->kind == LBM_INIT_QUADRANT) {
     const int ns = d->kind == LBM_INIT_HALF ? 2 : 4;
     for (int r = 0; r < ns; ++r) {
@@ -387,10 +416,14 @@ lbm_status lbm_init_riemann(lbm_ctx* ctx, int32_t problem, const lbm_riemann_des
   } else {
     return fail(ctx, LBM_EINVAL, "lbm_init_riemann: bad kind");
   }
-  switch (ctx->prec) {
-    case LBM_F64: launch_init_t<double>(ctx, P, k); break;
-    case LBM_F32_DEV: launch_init_t<float>(ctx, P, k); break;
-    default: launch_init_t<__nv_bfloat16>(ctx, P, k); break;
+  if (ctx->dim == 1) {
+    launch_init_d1(ctx->prec, ctx->stat, ctx->buf[ctx->cur], P, ctx->plane, k, ctx->stream);
+  } else {
+    switch (ctx->prec) {
+      case LBM_F64: launch_init_t<double>(ctx, P, k); break;
+      case LBM_F32_DEV: launch_init_t<float>(ctx, P, k); break;
+      default: launch_init_t<__nv_bfloat16>(ctx, P, k); break;
+    }
   }
   CKL();
   ctx->launches += 1;
@@ -623,10 +656,14 @@ lbm_status lbm_moments(lbm_ctx* ctx, int32_t problem, double* n, double* ux, dou
     int k = 0;
     for (int a = 0; a < 6; ++a) o[a] = user[a] ? ctx->tmp + (k++) * cells : nullptr;
   }
-  switch (ctx->prec) {
-    case LBM_F64: launch_moments_p<double>(ctx, P, o, g); break;
-    case LBM_F32_DEV: launch_moments_p<float>(ctx, P, o, g); break;
-    default: launch_moments_p<__nv_bfloat16>(ctx, P, o, g); break;
+  if (ctx->dim == 1) {
+    launch_moments_d1(ctx->prec, ctx->stat, ctx->buf[ctx->cur], P, ctx->plane, o, ctx->partials, g, ctx->stream);
+  } else {
+    switch (ctx->prec) {
+      case LBM_F64: launch_moments_p<double>(ctx, P, o, g); break;
+      case LBM_F32_DEV: launch_moments_p<float>(ctx, P, o, g); break;
+      default: launch_moments_p<__nv_bfloat16>(ctx, P, o, g); break;
+    }
   }
   CKL();
   ctx->launches += 1;
@@ -662,12 +699,13 @@ lbm_status lbm_get_populations(lbm_ctx* ctx, int32_t problem, double* f, int32_t
   const int64_t cells = (int64_t)P.nx * P.ny;
   double* dst = f;
   if (!on_device) {
-    lbm_status s = ensure_tmp(ctx, 9 * cells);
+    lbm_status s = ensure_tmp(ctx, ctx->q * cells);
     if (s != LBM_OK) return s;
     dst = ctx->tmp;
   }
   const unsigned g = blocks_for(cells, 256);
-  switch (ctx->prec) {
+  if (ctx->dim == 1) launch_pop_d1(ctx->prec, true, ctx->buf[ctx->cur], P, ctx->plane, dst, ctx->stream);
+  else switch (ctx->prec) {
     case LBM_F64: get_pop_kernel<double><<<g, 256, 0, ctx->stream>>>((const double*)ctx->buf[ctx->cur], P, ctx->plane, dst); break;
     case LBM_F32_DEV: get_pop_kernel<float><<<g, 256, 0, ctx->stream>>>((const float*)ctx->buf[ctx->cur], P, ctx->plane, dst); break;
     default: get_pop_kernel<__nv_bfloat16><<<g, 256, 0, ctx->stream>>>((const __nv_bfloat16*)ctx->buf[ctx->cur], P, ctx->plane, dst); break;
@@ -675,7 +713,7 @@ lbm_status lbm_get_populations(lbm_ctx* ctx, int32_t problem, double* f, int32_t
   CKL();
   ctx->launches += 1;
   if (!on_device) {
-    CK(cudaMemcpyAsync(f, dst, sizeof(double) * 9 * cells, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(f, dst, sizeof(double) * ctx->q * cells, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
   }
   return LBM_OK;
@@ -688,13 +726,14 @@ lbm_status lbm_set_populations(lbm_ctx* ctx, int32_t problem, const double* f, i
   const int64_t cells = (int64_t)P.nx * P.ny;
   const double* src = f;
   if (!on_device) {
-    lbm_status s = ensure_tmp(ctx, 9 * cells);
+    lbm_status s = ensure_tmp(ctx, ctx->q * cells);
     if (s != LBM_OK) return s;
-    CK(cudaMemcpyAsync(ctx->tmp, f, sizeof(double) * 9 * cells, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->tmp, f, sizeof(double) * ctx->q * cells, cudaMemcpyHostToDevice, ctx->stream));
     src = ctx->tmp;
   }
   const unsigned g = blocks_for(cells, 256);
-  switch (ctx->prec) {
+  if (ctx->dim == 1) launch_pop_d1(ctx->prec, false, ctx->buf[ctx->cur], P, ctx->plane, (double*)src, ctx->stream);
+  else switch (ctx->prec) {
     case LBM_F64: set_pop_kernel<double><<<g, 256, 0, ctx->stream>>>((double*)ctx->buf[ctx->cur], P, ctx->plane, src); break;
     case LBM_F32_DEV: set_pop_kernel<float><<<g, 256, 0, ctx->stream>>>((float*)ctx->buf[ctx->cur], P, ctx->plane, src); break;
     default: set_pop_kernel<__nv_bfloat16><<<g, 256, 0, ctx->stream>>>((__nv_bfloat16*)ctx->buf[ctx->cur], P, ctx->plane, src); break;

@@ -39,6 +39,14 @@ void launch_step_surr_tc_f32(int rows, unsigned grid, cudaStream_t s, const Step
                              unsigned long long* counters, const void* wtc);
 void launch_step_surr_tc_bf16(int rows, unsigned grid, cudaStream_t s, const StepArgs& a,
                               unsigned long long* counters, const void* wtc);
+// d1v3 (prec 0 FP64, 1 FP32 deviations, 2 BF16 deviations; stat STAT_T0 or
+// STAT_MB): step, initial equilibrium, moments with per-block partial sums,
+// and populations to (get) or from FP64 buffers [3][nx]
+void launch_step_d1(int prec, int stat, unsigned grid, cudaStream_t s, const StepArgs& a);
+void launch_init_d1(int prec, int stat, void* f, const ProbDev& P, int64_t plane, const InitDesc& d, cudaStream_t s);
+void launch_moments_d1(int prec, int stat, const void* f, const ProbDev& P, int64_t plane, double* const o[6],
+                       double* partials, unsigned g, cudaStream_t s);
+void launch_pop_d1(int prec, bool get, void* f, const ProbDev& P, int64_t plane, double* buf, cudaStream_t s);
 void launch_step_f64(int stat, int rows, unsigned grid, cudaStream_t s, const StepArgs& a);
 void launch_step_f32(int stat, int rows, unsigned grid, cudaStream_t s, const StepArgs& a);
 void launch_step_bf16(int stat, int rows, unsigned grid, cudaStream_t s, const StepArgs& a);

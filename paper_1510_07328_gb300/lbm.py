@@ -145,13 +145,14 @@ def _ptr(a) -> int | None:
 # ---------------------------------------------------------------- C-ABI calls, same names
 
 
-def lbm_create(problems, stat="fd", prec="f64", inv="exact", stream=None):
-    """problems: list of dicts with nx, ny, tau, bc_x, bc_y, n_ref, t_ref."""
+def lbm_create(problems, stat="fd", prec="f64", inv="exact", stream=None, dim=2):
+    """problems: list of dicts with nx, ny, tau, bc_x, bc_y, n_ref, t_ref;
+    dim 2: d2v9, dim 1: d1v3 (ny = 1)."""
     arr = (lbm_problem * len(problems))()
     for i, p in enumerate(problems):
         arr[i] = lbm_problem(int(p["nx"]), int(p["ny"]), float(p["tau"]), BC[p.get("bc_x", "periodic")],
                              BC[p.get("bc_y", "periodic")], float(p.get("n_ref", 1.0)), float(p.get("t_ref", 0.05)))
-    par = lbm_params(2, 3, STAT[stat], PREC[prec], LBM_INV_EXACT if inv == "exact" else LBM_INV_SURROGATE,
+    par = lbm_params(int(dim), 3, STAT[stat], PREC[prec], LBM_INV_EXACT if inv == "exact" else LBM_INV_SURROGATE,
                      len(problems), arr)
     ctx = C.c_void_p()
     _check(LIB.lbm_create(C.byref(par), C.c_void_p(stream or 0), C.byref(ctx)), None)
@@ -327,15 +328,16 @@ class Lattice:
     """One context over a list of problems (``inputs.Problem`` objects)."""
 
     def __init__(self, problems, stat="fd", prec="f64", stream=None, t_ref=None, n_ref=None, inv="exact",
-                 surrogate=None):
+                 surrogate=None, dim=2):
         self.problems = list(problems)
+        self.q = 9 if dim == 2 else 3
         descs = []
         for p in self.problems:
             tr = t_ref if t_ref is not None else float(np.median(p.t)) if stat == "fd" else 0.05
             nr = n_ref if n_ref is not None else float(np.mean(p.n))
             descs.append(dict(nx=p.nx, ny=p.ny, tau=p.tau, bc_x=p.bc_x, bc_y=p.bc_y, n_ref=nr,
                               t_ref=min(max(tr, 1e-3), 10.0)))
-        self.ctx = lbm_create(descs, stat, prec, inv=inv, stream=stream)
+        self.ctx = lbm_create(descs, stat, prec, inv=inv, stream=stream, dim=dim)
         self.stat = stat
         if surrogate is not None:
             lbm_surrogate_load(self.ctx, surrogate)
@@ -355,7 +357,7 @@ class Lattice:
 
     def populations(self, i: int = 0) -> np.ndarray:
         p = self.problems[i]
-        f = np.empty((9, p.ny, p.nx))
+        f = np.empty((self.q, p.ny, p.nx))
         lbm_get_populations(self.ctx, i, f)
         return f
 

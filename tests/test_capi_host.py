@@ -84,3 +84,22 @@ def test_create_rejects_unsupported_and_null(lib):
     assert lib.LIB.lbm_step(None, 1) == lib.LBM_EINVAL
     assert lib.LIB.lbm_destroy(None) == lib.LBM_OK
     assert lib.LIB.lbm_launch_count(None) == 0
+
+
+def test_create_rejects_d1v3_misuse(lib):
+    """d1v3 has no finite-temperature closure and its problems are one row."""
+    import ctypes as C
+
+    ctx = C.c_void_p()
+    arr = (lib.lbm_problem * 1)(lib.lbm_problem(64, 1, 0.8, 0, 0, 1.0, 0.05))
+    par = lib.lbm_params(1, 3, lib.STAT["fd"], 0, 0, 1, arr)
+    assert lib.LIB.lbm_create(C.byref(par), None, C.byref(ctx)) == lib.LBM_EUNSUPPORTED
+    assert "d1v3" in lib.lbm_last_error(None)
+    par = lib.lbm_params(1, 3, lib.STAT["t0"], 1, 1, 1, arr)  # learned inversion
+    assert lib.LIB.lbm_create(C.byref(par), None, C.byref(ctx)) == lib.LBM_EUNSUPPORTED
+    arr2 = (lib.lbm_problem * 1)(lib.lbm_problem(64, 2, 0.8, 0, 0, 1.0, 0.05))
+    par = lib.lbm_params(1, 3, lib.STAT["t0"], 0, 0, 1, arr2)
+    assert lib.LIB.lbm_create(C.byref(par), None, C.byref(ctx)) == lib.LBM_EINVAL
+    assert "ny = 1" in lib.lbm_last_error(None)
+    par = lib.lbm_params(0, 3, lib.STAT["t0"], 0, 0, 1, arr)
+    assert lib.LIB.lbm_create(C.byref(par), None, C.byref(ctx)) == lib.LBM_EUNSUPPORTED
