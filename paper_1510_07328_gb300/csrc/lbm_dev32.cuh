@@ -78,10 +78,11 @@ struct CellMom {
 __device__ __forceinline__ CellMom dev_moments(const ProbDev& P, const float g[9]) {
   CellMom m;
   const float nref = P.f.n_ref, ndref = P.f.ndelta_ref;
-  m.dn = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+  const float s56 = g[5] + g[6], s78 = g[7] + g[8], sd = s56 + s78;  // diagonal sums, shared
+  m.dn = (g[0] + ((g[1] + g[2]) + (g[3] + g[4]))) + sd;
   const float jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
-  const float jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
-  const float G1 = g[0] - ((g[5] + g[6]) + (g[7] + g[8]));
+  const float jy = (g[2] - g[4]) + (s56 - s78);
+  const float G1 = g[0] - sd;
   m.n = nref + m.dn;
   m.in = __fdividef(1.0f, m.n);
   m.ux = jx * m.in;
@@ -93,6 +94,10 @@ __device__ __forceinline__ CellMom dev_moments(const ProbDev& P, const float g[9
 }
 
 // Equilibrium and BGK of one cell given J_2, J_4; stores at `off`.
+//
+// The moving populations come in opposite pairs (e_a' = -e_a), and
+// S(+-eu) = (Q + a_2 eu^2) +- eu (a_1 + b_0 C + b_0 k_4 eu^2): one even and one
+// odd part per pair.
 template <class T, int STAT>
 __device__ __forceinline__ void relax_store_dev(const ProbDev& P, const float g[9], const CellMom& m, float J2,
                                                 float J4, T* __restrict__ fout, int64_t plane, int off) {
@@ -113,26 +118,32 @@ __device__ __forceinline__ void relax_store_dev(const ProbDev& P, const float g[
   const float D22 = __fdividef(1.0f, 2.0f - J2);
   const float D42 = __fdividef(1.0f, 3.0f - 2.0f * J4);
   const float iJ2 = __fdividef(1.0f, J2);
-  const float a1 = 3.0f * iJ2, a2 = 4.5f * iJ2, b0 = 1.5f * iJ2;
-  const float a3 = 2.25f * (D22 - 1.0f) * iJ2;
-  const float a4 = 1.5f * D22;
-  const float omJ = 1.0f - J2;
-  const float k0 = 4.0f * omJ * J4 * D42, k1 = 3.0f * omJ * J4 * D42, k2 = 3.0f * J4 * D42;
-  const float k3 = 2.25f * J4 * (D42 - 1.0f), k4 = 3.0f * J4;
-  const float C1 = k0 - k1 + (k3 - k2) * u2, C2 = k0 - 2.0f * k1 + (2.0f * k3 - k2) * u2;
-  const float Q0 = -a4 * u2, Q1 = (a3 - a4) * u2, Q2 = (2.0f * a3 - a4) * u2;
-  auto Sm1 = [&](float eu, float C, float Qc) { return Qc + eu * (a1 + a2 * eu + b0 * (C + k4 * eu * eu)); };
-  float ge[9];
-  ge[0] = dW0 + W0 * Q0;
-  ge[1] = dWs + Ws * Sm1(ux, C1, Q1);
-  ge[2] = dWs + Ws * Sm1(uy, C1, Q1);
-  ge[3] = dWs + Ws * Sm1(-ux, C1, Q1);
-  ge[4] = dWs + Ws * Sm1(-uy, C1, Q1);
-  ge[5] = dWl + Wl * Sm1(ux + uy, C2, Q2);
-  ge[6] = dWl + Wl * Sm1(-ux + uy, C2, Q2);
-  ge[7] = dWl + Wl * Sm1(-ux - uy, C2, Q2);
-  ge[8] = dWl + Wl * Sm1(ux - uy, C2, Q2);
+  // The bracket's constants, with t = J_4 Delta_4^2 and P = (1 - J_2) t:
+  //   C_short = P - (3/4 t + 9/4 J_4) u^2,  C_long = -2 P + (3/2 t - 9/2 J_4) u^2,
+  //   A = a_1 + b_0 C (a_1 = 3/J_2, b_0 = 3/(2 J_2)),  b_0 k_4 = 9 J_4/(2 J_2),
+  //   Q_rest = -3/2 Delta_2^2 u^2,  Q_short = (9/4 r - 3/2 Delta_2^2) u^2,
+  //   Q_long = (9/2 r - 3/2 Delta_2^2) u^2,  r = (Delta_2^2 - 1)/J_2.
+  const float t = J4 * D42, Pt = (1.0f - J2) * t;
+  const float A1 = iJ2 * fmaf(-fmaf(1.125f, t, 3.375f * J4), u2, fmaf(1.5f, Pt, 3.0f));
+  const float A2 = iJ2 * fmaf(fmaf(2.25f, t, -6.75f * J4), u2, fmaf(-3.0f, Pt, 3.0f));
+  const float bk = 4.5f * J4 * iJ2, a2 = 4.5f * iJ2;
+  const float h = 1.5f * D22, r = (D22 - 1.0f) * iJ2;
+  const float Q0 = -h * u2, Q1 = fmaf(2.25f, r, -h) * u2, Q2 = fmaf(4.5f, r, -h) * u2;
   const float w = P.f.omega;
+  // even and odd parts per opposite pair: g_eq(+-eu) = base +- wo
+  float ge[9];
+  ge[0] = fmaf(W0, Q0, dW0);
+  auto pair = [&](float eu, float A, float Qc, float W, float dW, int ap, int am) {
+    const float e2 = eu * eu;
+    const float base = fmaf(W, fmaf(a2, e2, Qc), dW);
+    const float wo = W * (eu * fmaf(bk, e2, A));
+    ge[ap] = base + wo;
+    ge[am] = base - wo;
+  };
+  pair(ux, A1, Q1, Ws, dWs, 1, 3);
+  pair(uy, A1, Q1, Ws, dWs, 2, 4);
+  pair(ux + uy, A2, Q2, Wl, dWl, 5, 7);
+  pair(ux - uy, A2, Q2, Wl, dWl, 8, 6);
 #pragma unroll
   for (int a = 0; a < 9; ++a) fout[a * plane + off] = Dev<T>::st(fmaf(w, ge[a] - g[a], g[a]));
 }
@@ -189,7 +200,7 @@ __device__ __forceinline__ int gather_dev(const T* __restrict__ fin, int64_t pla
 // The next row's nine loads are issued before the current row's collision so
 // that each thread keeps two rows of loads in flight.
 template <class T, int STAT, int TY, bool PERSIST>
-__global__ void __launch_bounds__(kTileX, 10) stream_collide_dev(const T* __restrict__ fin, T* __restrict__ fout,
+__global__ void __launch_bounds__(kTileX, sizeof(T) == 4 ? 8 : 10) stream_collide_dev(const T* __restrict__ fin, T* __restrict__ fout,
                                                                  const ProbDev* __restrict__ probs, int nprob,
                                                                  int ntiles, int64_t plane, InvLimitsF L) {
   int tile = (int)blockIdx.x;
