@@ -16,4 +16,8 @@ Modules:
           FD inversion, BGK step (d2v9)
   lbm1d   the d1v3 lattice with the zero-temperature and Maxwell-Boltzmann
           closures
+  porous  rigid obstacles (halfway bounce-back) and a constant body force
+          (exact difference method)
+  riemann exact isothermal Riemann solution (the Fig. 1 comparison)
+  mlp     the learned inversion's features, targets, forward pass and gradient
 """

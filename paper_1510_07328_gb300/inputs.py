@@ -224,6 +224,58 @@ def random_field(nx: int, ny: int, seed: int, tau: float = 0.7, bc_x: str = "per
     return Problem(nx, ny, tau, bc_x, bc_y, n, ux, uy, t, name=f"random_{nx}x{ny}", kind="field")
 
 
+def disc_centres(nx: int, ny: int, count: int, radius: int, seed: int) -> list:
+    """Integer centres of `count` discs in an nx x ny periodic box, drawn
+    uniformly (SplitMix64, seed) and rejected when closer than 2 radius + 1 to
+    an earlier centre (periodic distance), so the discs neither overlap nor
+    touch."""
+    out = []
+    k = 0
+    while len(out) < count:
+        if k > 10000 * count:
+            raise ValueError("no room for the discs")
+        r = uniform(seed, 2, offset=2 * k)
+        k += 1
+        cx, cy = min(int(r[0] * nx), nx - 1), min(int(r[1] * ny), ny - 1)
+        ok = True
+        for ox, oy in out:
+            dx, dy = abs(cx - ox), abs(cy - oy)
+            dx, dy = min(dx, nx - dx), min(dy, ny - dy)
+            if dx * dx + dy * dy < (2 * radius + 1) ** 2:
+                ok = False
+                break
+        if ok:
+            out.append((cx, cy))
+    return out
+
+
+def disc_mask(nx: int, ny: int, centres, radius: float) -> np.ndarray:
+    """Solid mask (ny, nx) of discs: cell (x, y) is solid when its periodic
+    distance to a centre is at most the radius."""
+    ys, xs = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    solid = np.zeros((ny, nx), dtype=bool)
+    for cx, cy in centres:
+        dx = np.abs(xs - cx)
+        dy = np.abs(ys - cy)
+        dx = np.minimum(dx, nx - dx)
+        dy = np.minimum(dy, ny - dy)
+        solid |= dx * dx + dy * dy <= radius * radius
+    return solid
+
+
+def porous_medium(nx: int = 700, ny: int = 150, count: int = 30, radius: int = 3, seed: int = 12,
+                  tau: float = 0.7, n0: float = 1.0, t: float = 0.5):
+    """The paper's porous sample: `count` discs of the given radius at seeded
+    random positions in a periodic nx x ny box, fluid at rest with density
+    n0 (and t = T/T_F for the FD closure).  Returns (Problem, solid mask)."""
+    solid = disc_mask(nx, ny, disc_centres(nx, ny, count, radius, seed), radius)
+    n = np.full((ny, nx), n0)
+    z = np.zeros((ny, nx))
+    p = Problem(nx, ny, tau, "periodic", "periodic", n, z, z.copy(), np.full((ny, nx), t),
+                name=f"porous_{nx}x{ny}_{count}discs", kind="field")
+    return p, solid
+
+
 def perturb_populations(f: np.ndarray, seed: int, amp: float) -> np.ndarray:
     """Multiply populations by (1 + amp * U[-1, 1]) to leave equilibrium."""
     r = uniform(seed, f.size).reshape(f.shape)
