@@ -48,9 +48,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="f32", choices=["f32", "bf16", "f64"])
     ap.add_argument("--L", type=int, default=4096)
-    ap.add_argument("--workload", default="smooth_t", choices=["smooth_t", "batched", "d1v3"],
+    ap.add_argument("--workload", default="smooth_t", choices=["smooth_t", "batched", "d1v3", "porous"],
                     help="smooth_t: one 4096^2 lattice; batched: 256 uneven quasi-1D Riemann problems; "
-                         "d1v3: the zero-temperature Riemann run of the paper's Fig. 1 on d1v3, scaled to --cells1d")
+                         "d1v3: the zero-temperature Riemann run of the paper's Fig. 1 on d1v3, scaled to --cells1d; "
+                         "porous: the paper's porous sample (porosity 0.992, discs of radius 3) scaled to L x L")
     ap.add_argument("--cells1d", type=int, default=1 << 25, help="lattice length of the d1v3 workload")
     ap.add_argument("--autotune", action="store_true", help="autotune the tiling before timing (always on for batched)")
     ap.add_argument("--inv", default="exact", choices=["exact", "surrogate"],
@@ -64,7 +65,28 @@ def parse():
     return ap.parse_args()
 
 
+def porous_discs(L: int) -> int:
+    """Discs of radius 3 for the porous sample's porosity (30 in 700 x 150) on L x L."""
+    return int(round(30 * L * L / (700 * 150)))
+
+
 def workload_config(a, world, probs=None, tiling=None):
+    if a.workload == "porous":
+        return {
+            "workload": f"porous_{a.L}x{a.L}",
+            "lattice": [a.L, a.L],
+            "cells": a.L * a.L,
+            "stencil": "d2v9 K=3 LBGK with rigid obstacles (halfway bounce-back) and an exact-difference body force, "
+                       + {"mb": "Maxwell-Boltzmann closure", "t0": "theta = 0 closure", "fd": "FD closure"}[a.stat],
+            "storage": {"f32": "FP32 deviations g = f - W_ref", "bf16": "BF16 deviations", "f64": "FP64 f"}[a.prec],
+            "obstacles": f"{porous_discs(a.L)} discs of radius 3 at seeded positions (porosity 0.992, as the paper's "
+                         "700 x 150 sample with 30 discs)",
+            "force": [1e-6, 0.0],
+            "tau": 0.7,
+            "boundaries": "periodic",
+            "l2": f"inputs larger than L2 ({2 * 9 * a.L * a.L * BYTES_PER_ELEM[a.prec] / 1e9:.2f} GB population buffers)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+        }
     if a.workload == "d1v3":
         return {
             "workload": f"d1v3_riemann_{a.cells1d}",
@@ -214,6 +236,7 @@ KERNEL_SOURCES = {
     "stream_collide_dev": _EXACT_SRC + ("step_f32.cu", "step_bf16.cu"),
     "stream_collide_f64": ("lbm_kernels.cuh", "fd_device.cuh", "fd_device_f32.cuh", "launch.h", "step_f64.cu"),
     "stream_collide_surr": _EXACT_SRC + ("surrogate.cuh", "tc_sm100.cuh", "lbm_surr.cuh", "step_surr.cu"),
+    "stream_collide_porous": _EXACT_SRC + ("lbm_porous.cuh", "step_porous.cu"),
     "stream_collide_d1": ("lbm_kernels.cuh", "fd_device.cuh", "fd_device_f32.cuh", "launch.h", "lbm_d1.cuh",
                           "step_d1.cu"),
 }
@@ -319,6 +342,19 @@ def run_ours(a, world, rank, local):
         prob = None
         dev_fields = None
         lat = lbm.Lattice(probs, stat=a.stat, prec=a.prec, stream=stream.cuda_stream, n_ref=1.2, t_ref=0.05)
+    elif a.workload == "porous":
+        if a.stat == "fd":
+            a.stat = "mb"  # the closure that is stable at tau = 0.7 around obstacles
+        centres = inputs.disc_centres(a.L, a.L, porous_discs(a.L), 3, 13)
+        solid = inputs.disc_mask(a.L, a.L, centres, 3)
+        prob = inputs.Problem(a.L, a.L, 0.7, "periodic", "periodic", np.ones((a.L, a.L)), np.zeros((a.L, a.L)),
+                              np.zeros((a.L, a.L)), np.full((a.L, a.L), 0.5), name=f"porous_{a.L}", kind="field")
+        probs = [prob]
+        dev_fields = {k: torch.from_numpy(getattr(prob, k)).cuda() for k in ("n", "ux", "uy", "t")}
+        torch.cuda.synchronize()
+        lat = lbm.Lattice(probs, stat=a.stat, prec=a.prec, stream=stream.cuda_stream, n_ref=1.0, t_ref=0.5)
+        lat.set_obstacles(solid)
+        lat.set_force(1e-6, 0.0)
     elif a.workload == "d1v3":
         if a.stat == "fd":
             a.stat = "t0"  # d1v3 has no finite-temperature closure
@@ -409,13 +445,16 @@ def run_ours(a, world, rank, local):
 
     value = world * cells * a.steps / (ms_max / 1e3) / 1e6
     per_launch_s = ms / 1e3 / a.steps
-    bytes_per_cell = (6 if a.workload == "d1v3" else 18) * BYTES_PER_ELEM[a.prec]
+    bytes_per_cell = (6 if a.workload == "d1v3" else 18) * BYTES_PER_ELEM[a.prec] + (1 if a.workload == "porous" else 0)
     achieved = bytes_per_cell * cells / per_launch_s / 1e9
     peak, peak_kind = peaks()
     kname = {"f32": "stream_collide_dev<float,%s>", "bf16": "stream_collide_dev<bf16,%s>",
              "f64": "stream_collide_f64<%s>"}[a.prec] % a.stat.upper()
     if a.inv == "surrogate":
         kname = {"f32": "stream_collide_surr_tc<float>", "bf16": "stream_collide_surr_tc<bf16>"}[a.prec]
+    if a.workload == "porous":
+        kname = "stream_collide_porous<%s,%s>" % ({"f32": "float", "bf16": "bf16", "f64": "double"}[a.prec],
+                                                  a.stat.upper())
     if a.workload == "d1v3":
         kname = "stream_collide_d1<%s,%s>" % ({"f32": "float", "bf16": "bf16", "f64": "double"}[a.prec],
                                               a.stat.upper())

@@ -192,6 +192,31 @@ lbm_status lbm_moments(lbm_ctx* ctx, int32_t problem, double* n, double* ux, dou
 lbm_status lbm_get_populations(lbm_ctx* ctx, int32_t problem, double* f, int32_t on_device);
 lbm_status lbm_set_populations(lbm_ctx* ctx, int32_t problem, const double* f, int32_t on_device);
 
+/* Rigid obstacles and a constant body force (the porous-medium experiment of
+ * Sect. "Numerical simulations for electrons in metals": electrons driven by
+ * an external force through rigid obstacles, bounce-back on the obstacles).
+ *
+ * lbm_set_obstacles: solid = nx*ny bytes, row-major [ny][nx], nonzero marks a
+ * solid cell; host or device memory per on_device, read during the call
+ * only; NULL removes the problem's obstacles.  A fluid cell whose pull source
+ * is solid takes the opposite population of its own cell (halfway
+ * bounce-back, as at the walls); solid cells are not updated and
+ * lbm_moments reports them as n = u = T = mu = t = 0, outside the diag sums.
+ * The first call allocates one byte per cell of the context.
+ *
+ * lbm_set_force: force (fx, fy) per cell and step in lattice units, applied
+ * by the exact difference method: after the BGK relaxation each fluid cell
+ * receives f_eq(n, u_0 + F/n) - f_eq(n, u_0) on the same moments, which adds
+ * exactly F of momentum and no mass.  lbm_moments then reports the velocity
+ * at the time level, (j + F/2)/n.  With the FD closure the work of the force
+ * heats the gas (the energy moment is conserved by the collision only).
+ *
+ * Both need d2v9 and the exact inversion (else LBM_EUNSUPPORTED), synchronise
+ * the stream and drop captured graphs.  Errors: LBM_EINVAL (index, non-finite
+ * force), LBM_EUNSUPPORTED, LBM_ENOMEM, LBM_ECUDA. */
+lbm_status lbm_set_obstacles(lbm_ctx* ctx, int32_t problem, const uint8_t* solid, int32_t on_device);
+lbm_status lbm_set_force(lbm_ctx* ctx, int32_t problem, double fx, double fy);
+
 /* Release everything the context owns (synchronises its stream first). */
 lbm_status lbm_destroy(lbm_ctx* ctx);
 

@@ -112,6 +112,8 @@ struct lbm_ctx {
   ProbDev* pd = nullptr;
   int64_t plane = 0, ntiles = 0;
   int dim = 2, q = 9;        // lattice: d2v9 or d1v3
+  uint8_t* mask = nullptr;   // device: obstacle mask indexed like the cells (allocated on first use)
+  bool porous = false;       // some problem has obstacles or a body force
   int rows = kTileYDefault;  // rows per tile
   int ctas = 0;              // 0: one CTA per tile; else a persistent grid of this many CTAs
   void* buf[2] = {nullptr, nullptr};
@@ -167,6 +169,10 @@ void launch_step(lbm_ctx* c, const void* in, void* out, cudaStream_t s) {
   const unsigned grid = c->ctas > 0 ? (unsigned)std::min<int64_t>(c->ctas, c->ntiles) : (unsigned)c->ntiles;
   if (c->dim == 1) {
     launch_step_d1(c->prec, c->stat, grid, s, a);
+    return;
+  }
+  if (c->porous) {
+    launch_step_porous(c->prec, c->stat, c->rows, grid, s, a);
     return;
   }
   if (c->inv == LBM_INV_SURROGATE) {
@@ -744,6 +750,61 @@ lbm_status lbm_set_populations(lbm_ctx* ctx, int32_t problem, const double* f, i
   return LBM_OK;
 }
 
+namespace {
+
+// Re-upload the problem table after a host-side change and pick the step kernel.
+lbm_status upload_problems(lbm_ctx* ctx) {
+  ctx->porous = false;
+  for (const ProbDev& P : ctx->ph) ctx->porous = ctx->porous || P.solid != nullptr || P.fx != 0.0 || P.fy != 0.0;
+  CK(cudaMemcpyAsync(ctx->pd, ctx->ph.data(), sizeof(ProbDev) * ctx->nprob, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  drop_graphs(ctx);
+  return LBM_OK;
+}
+
+lbm_status porous_allowed(lbm_ctx* ctx, const char* who) {
+  if (ctx->dim != 2) return fail(ctx, LBM_EUNSUPPORTED, std::string(who) + ": obstacles and forces need d2v9");
+  if (ctx->inv != LBM_INV_EXACT)
+    return fail(ctx, LBM_EUNSUPPORTED, std::string(who) + ": obstacles and forces need the exact inversion");
+  return LBM_OK;
+}
+
+}  // namespace
+
+lbm_status lbm_set_obstacles(lbm_ctx* ctx, int32_t problem, const uint8_t* solid, int32_t on_device) {
+  if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_set_obstacles: NULL context");
+  if (problem < 0 || problem >= ctx->nprob) return fail(ctx, LBM_EINVAL, "lbm_set_obstacles: bad problem index");
+  lbm_status st = porous_allowed(ctx, "lbm_set_obstacles");
+  if (st != LBM_OK) return st;
+  ProbDev& P = ctx->ph[problem];
+  if (!solid) {
+    P.solid = nullptr;
+    return upload_problems(ctx);
+  }
+  if (!ctx->mask) {
+    CK(cudaMalloc(&ctx->mask, (size_t)ctx->plane));
+    CK(cudaMemsetAsync(ctx->mask, 0, (size_t)ctx->plane, ctx->stream));
+  }
+  CK(cudaMemcpy2DAsync(ctx->mask + P.base, (size_t)P.pitch, solid, (size_t)P.nx, (size_t)P.nx, (size_t)P.ny,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  P.solid = ctx->mask;
+  return upload_problems(ctx);
+}
+
+lbm_status lbm_set_force(lbm_ctx* ctx, int32_t problem, double fx, double fy) {
+  if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_set_force: NULL context");
+  if (problem < 0 || problem >= ctx->nprob) return fail(ctx, LBM_EINVAL, "lbm_set_force: bad problem index");
+  if (!std::isfinite(fx) || !std::isfinite(fy)) return fail(ctx, LBM_EINVAL, "lbm_set_force: non-finite force");
+  lbm_status st = porous_allowed(ctx, "lbm_set_force");
+  if (st != LBM_OK) return st;
+  ProbDev& P = ctx->ph[problem];
+  P.fx = fx;
+  P.fy = fy;
+  P.f.fx = (float)fx;
+  P.f.fy = (float)fy;
+  return upload_problems(ctx);
+}
+
 lbm_status lbm_destroy(lbm_ctx* ctx) {
   if (!ctx) return LBM_OK;
   cudaStreamSynchronize(ctx->stream);
@@ -759,6 +820,7 @@ lbm_status lbm_destroy(lbm_ctx* ctx) {
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
   if (ctx->surr_count) cudaFree(ctx->surr_count);
   if (ctx->wtc) cudaFree(ctx->wtc);
+  if (ctx->mask) cudaFree(ctx->mask);
   delete ctx->surr;
   delete ctx;
   return LBM_OK;

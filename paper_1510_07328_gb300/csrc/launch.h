@@ -47,6 +47,8 @@ void launch_init_d1(int prec, int stat, void* f, const ProbDev& P, int64_t plane
 void launch_moments_d1(int prec, int stat, const void* f, const ProbDev& P, int64_t plane, double* const o[6],
                        double* partials, unsigned g, cudaStream_t s);
 void launch_pop_d1(int prec, bool get, void* f, const ProbDev& P, int64_t plane, double* buf, cudaStream_t s);
+// d2v9 with obstacles (ProbDev::solid) and a body force (ProbDev::fx, fy)
+void launch_step_porous(int prec, int stat, int rows, unsigned grid, cudaStream_t s, const StepArgs& a);
 void launch_step_f64(int stat, int rows, unsigned grid, cudaStream_t s, const StepArgs& a);
 void launch_step_f32(int stat, int rows, unsigned grid, cudaStream_t s, const StepArgs& a);
 void launch_step_bf16(int stat, int rows, unsigned grid, cudaStream_t s, const StepArgs& a);

@@ -31,7 +31,10 @@ struct ProbDev {
   struct {
     float omega, n_ref, ndelta_ref;
     float wref[3];  // rest, short, long
+    float fx, fy;
   } f;              // FP32 copies for the reduced-precision step
+  const uint8_t* solid;              // obstacle mask indexed like the cells (nonzero: solid), or null
+  double fx, fy;                     // constant body force per cell and step
 };
 
 // Closure constants of the statistics without inversion.
@@ -331,9 +334,15 @@ __global__ void __launch_bounds__(kMomThreads) moments_kernel(const T* __restric
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t cells = (int64_t)P.nx * P.ny;
   double acc[kNPartial] = {0, 0, 0, 0, 0, 0};
-  if (i < cells) {
-    const int y = (int)(i / P.nx), x = (int)(i % P.nx);
-    const int64_t c = P.base + (int64_t)y * P.pitch + x;
+  const int64_t c = i < cells ? P.base + (int64_t)(i / P.nx) * P.pitch + (int)(i % P.nx) : 0;
+  if (i < cells && P.solid != nullptr && P.solid[c] != 0) {  // obstacle: no fluid
+    if (on) on[i] = 0.0;
+    if (oux) oux[i] = 0.0;
+    if (ouy) ouy[i] = 0.0;
+    if (oT) oT[i] = 0.0;
+    if (omu) omu[i] = 0.0;
+    if (ot) ot[i] = 0.0;
+  } else if (i < cells) {
     double v[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) v[a] = Stor<T>::to_f64(f[a * plane + c], Stor<T>::dev ? P.wref[a] : 0.0);
@@ -357,8 +366,8 @@ __global__ void __launch_bounds__(kMomThreads) moments_kernel(const T* __restric
       theta = mu = t = __longlong_as_double(0x7ff8000000000000LL);
     }
     if (on) on[i] = n;
-    if (oux) oux[i] = ux;
-    if (ouy) ouy[i] = uy;
+    if (oux) oux[i] = (jx + 0.5 * P.fx) / n;  // velocity at the time level under a body force
+    if (ouy) ouy[i] = (jy + 0.5 * P.fy) / n;
     if (oT) oT[i] = theta;
     if (omu) omu[i] = mu;
     if (ot) ot[i] = t;

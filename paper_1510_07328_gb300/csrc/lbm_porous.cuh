@@ -1,0 +1,172 @@
+// The d2v9 step with rigid obstacles and a constant body force (the paper's
+// porous-medium experiment, Sect. "Numerical simulations for electrons in
+// metals").  Obstacles: a fluid cell whose pull source is solid (or beyond a
+// wall) takes the opposite population of its own cell (halfway bounce-back);
+// solid cells are not updated.  Force: exact difference method (Kupershtokh,
+// Medvedev and Karpov 2009): after BGK every fluid cell receives
+// f_eq(n, u_0 + F/n) - f_eq(n, u_0) on the same moments (same J_2, J_4), which
+// adds exactly F of momentum and no mass.
+#pragma once
+#include "lbm_dev32.cuh"
+
+namespace lbm {
+
+__device__ __forceinline__ bool is_solid(const ProbDev& P, int64_t c) { return P.solid != nullptr && P.solid[c] != 0; }
+
+// Pull of the nine populations of cell (x, y) with obstacles.
+template <class T>
+__device__ __forceinline__ void pull9_obst(const T* __restrict__ fin, int64_t plane, const ProbDev& P, int x, int y,
+                                           T v[9]) {
+  const PullIdx q = pull_index(P, x, y);
+  auto ld = [&](int a, int64_t r, int xs, int opp) -> T {
+    return (r < 0 || xs < 0 || is_solid(P, r + xs)) ? fin[opp * plane + q.row + x] : fin[a * plane + r + xs];
+  };
+  v[0] = fin[q.row + x];
+  v[1] = ld(1, q.row, q.xm, 3);
+  v[2] = ld(2, q.rm, x, 4);
+  v[3] = ld(3, q.row, q.xp, 1);
+  v[4] = ld(4, q.rp, x, 2);
+  v[5] = ld(5, q.rm, q.xm, 7);
+  v[6] = ld(6, q.rm, q.xp, 8);
+  v[7] = ld(7, q.rp, q.xp, 5);
+  v[8] = ld(8, q.rp, q.xm, 6);
+}
+
+// FP64: BGK on f_eq(n, u) plus f_eq(n, u + F/n) - f_eq(n, u).
+template <int STAT>
+__device__ __forceinline__ void collide_force_f64(const ProbDev& P, const double f[9], double* __restrict__ fout,
+                                                  int64_t plane, int64_t c, const InvLimits& L, const InvLimitsF& Lf) {
+  const double n = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+  const double jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+  const double jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+  const double E = ((f[1] + f[2]) + (f[3] + f[4])) + 2.0 * ((f[5] + f[6]) + (f[7] + f[8]));
+  const double in = 1.0 / n;
+  const double ux = jx * in, uy = jy * in;
+  double J2, J4;
+  if (STAT == STAT_FD) {
+    J2 = 1.5 * (E * in - (ux * ux + uy * uy));
+    int cl;
+    double xx;
+    J4 = j4_fp64(J2, L, Lf, &xx, &cl);
+  } else {
+    J2 = FixedJ<STAT>::j2;
+    J4 = FixedJ<STAT>::j4;
+  }
+  double fe[9], ff[9];
+  feq_f64(n, ux, uy, J2, J4, fe);
+  feq_f64(n, ux + P.fx * in, uy + P.fy * in, J2, J4, ff);
+  const double w = P.omega;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) fout[a * plane + c] = fma(w, fe[a] - f[a], f[a]) + (ff[a] - fe[a]);
+}
+
+// FP32 deviations: BGK as in relax_store_dev plus the force term, whose
+// difference S(u + d) - S(u) (d = F/n) is expanded exactly, so that a small
+// force loses no precision to cancellation.  With p = e.u, q = e.d,
+// s = |u|^2, r = 2 u.d + |d|^2 and the class constants of the bracket
+// (Q = q_c s, C = c_0 + c_1 s, A = a_1 + b_0 C):
+//   S(+-e)(u + d) - S(+-e)(u) = even +- odd,
+//   even = q_c r + a_2 q (2 p + q),
+//   odd  = q (A + b_0 c_1 r) + b_0 c_1 p r + b_0 k_4 q (p'^2 + p' p + p^2),  p' = p + q;
+// the rest population gets q_rest r.
+template <class T, int STAT>
+__device__ __forceinline__ void relax_force_store_dev(const ProbDev& P, const float g[9], const CellMom& m, float J2,
+                                                      float J4, T* __restrict__ fout, int64_t plane, int off) {
+  const float dn = m.dn, X = m.X, ux = m.ux, uy = m.uy, u2 = m.u2;
+  float dW0, dWs, dWl;
+  if (STAT == STAT_FD) {
+    dW0 = dn * (1.0f / 6.0f) + (5.0f / 6.0f) * X;
+    dWs = (dn - X) * (1.0f / 6.0f);
+    dWl = 0.25f * dWs;
+  } else {
+    dW0 = dn * (1.0f - 5.0f * J2 / 9.0f);
+    dWs = dn * J2 / 9.0f;
+    dWl = dn * J2 / 36.0f;
+  }
+  const float W0 = P.f.wref[0] + dW0, Ws = P.f.wref[1] + dWs, Wl = P.f.wref[2] + dWl;
+  const float D22 = __fdividef(1.0f, 2.0f - J2);
+  const float D42 = __fdividef(1.0f, 3.0f - 2.0f * J4);
+  const float iJ2 = __fdividef(1.0f, J2);
+  const float t = J4 * D42, Pt = (1.0f - J2) * t;
+  const float b0 = 1.5f * iJ2;
+  const float c1s = -fmaf(0.75f, t, 2.25f * J4), c1l = fmaf(1.5f, t, -4.5f * J4);
+  const float A1 = iJ2 * fmaf(-fmaf(1.125f, t, 3.375f * J4), u2, fmaf(1.5f, Pt, 3.0f));
+  const float A2 = iJ2 * fmaf(fmaf(2.25f, t, -6.75f * J4), u2, fmaf(-3.0f, Pt, 3.0f));
+  const float bk = 4.5f * J4 * iJ2, a2 = 4.5f * iJ2;
+  const float h = 1.5f * D22, r = (D22 - 1.0f) * iJ2;
+  const float q0 = -h, q1 = fmaf(2.25f, r, -h), q2 = fmaf(4.5f, r, -h);
+  const float w = P.f.omega;
+  // force: d = F/n, rr = 2 u.d + |d|^2
+  const float dx = P.f.fx * m.in, dy = P.f.fy * m.in;
+  const float rr = fmaf(2.0f, fmaf(ux, dx, uy * dy), fmaf(dx, dx, dy * dy));
+  float ge[9], gf[9];
+  ge[0] = fmaf(W0, q0 * u2, dW0);
+  gf[0] = W0 * (q0 * rr);
+  auto pair = [&](float eu, float ed, float A, float qc, float c1, float W, float dW, int ap, int am) {
+    const float e2 = eu * eu;
+    const float base = fmaf(W, fmaf(a2, e2, qc * u2), dW);
+    const float wo = W * (eu * fmaf(bk, e2, A));
+    ge[ap] = base + wo;
+    ge[am] = base - wo;
+    const float pp = eu + ed;
+    const float bc1 = b0 * c1;
+    const float even = fmaf(qc, rr, a2 * ed * fmaf(2.0f, eu, ed));
+    const float odd = fmaf(ed, fmaf(bc1, rr, A), fmaf(bc1 * eu, rr, bk * ed * fmaf(pp, pp + eu, e2)));
+    gf[ap] = W * (even + odd);
+    gf[am] = W * (even - odd);
+  };
+  pair(ux, dx, A1, q1, c1s, Ws, dWs, 1, 3);
+  pair(uy, dy, A1, q1, c1s, Ws, dWs, 2, 4);
+  pair(ux + uy, dx + dy, A2, q2, c1l, Wl, dWl, 5, 7);
+  pair(ux - uy, dx - dy, A2, q2, c1l, Wl, dWl, 8, 6);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) fout[a * plane + off] = Dev<T>::st(fmaf(w, ge[a] - g[a], g[a]) + gf[a]);
+}
+
+// One CTA per tile of 128 cells x TY rows (PERSIST: a smaller grid walks the
+// tiles).  T = double: FP64 populations; float / bf16: deviations.
+template <class T, int STAT, int TY, bool PERSIST>
+__global__ void __launch_bounds__(kTileX) stream_collide_porous(const T* __restrict__ fin, T* __restrict__ fout,
+                                                                const ProbDev* __restrict__ probs, int nprob,
+                                                                int ntiles, int64_t plane, InvLimits L,
+                                                                InvLimitsF Lf) {
+  int tile = (int)blockIdx.x;
+#pragma unroll 1
+  do {
+    const int p = nprob == 1 ? 0 : find_problem(probs, nprob, tile);
+    const ProbDev& P = probs[p];
+    const int lt = tile - (int)P.tile_begin;
+    const int ty = lt / P.tiles_x;
+    const int x = (lt - ty * P.tiles_x) * kTileX + (int)threadIdx.x;
+    if (x < P.nx) {
+      const int y1 = min(ty * TY + TY, P.ny);
+#pragma unroll 1
+      for (int y = ty * TY; y < y1; ++y) {
+        const int64_t c = P.base + (int64_t)y * P.pitch + x;
+        if (is_solid(P, c)) continue;
+        T v[9];
+        pull9_obst(fin, plane, P, x, y, v);
+        if constexpr (Stor<T>::dev) {
+          float g[9];
+#pragma unroll
+          for (int a = 0; a < 9; ++a) g[a] = Dev<T>::ld(v[a]);
+          const CellMom m = dev_moments(P, g);
+          float J2, J4;
+          if (STAT == STAT_FD) {
+            J2 = 1.5f - m.delta;
+            float xx;
+            J4 = j4_from_delta_f(m.delta, Lf, &xx);
+          } else {
+            J2 = (float)FixedJ<STAT>::j2;
+            J4 = (float)FixedJ<STAT>::j4;
+          }
+          relax_force_store_dev<T, STAT>(P, g, m, J2, J4, fout, plane, (int)c);
+        } else {
+          collide_force_f64<STAT>(P, v, fout, plane, c, L, Lf);
+        }
+      }
+    }
+  } while (PERSIST && (tile += (int)gridDim.x) < ntiles);
+}
+
+}  // namespace lbm

@@ -229,37 +229,39 @@ def disc_centres(nx: int, ny: int, count: int, radius: int, seed: int) -> list:
     uniformly (SplitMix64, seed) and rejected when closer than 2 radius + 1 to
     an earlier centre (periodic distance), so the discs neither overlap nor
     touch."""
-    out = []
+    cx = np.empty(count, dtype=np.int64)
+    cy = np.empty(count, dtype=np.int64)
+    m = 0
     k = 0
-    while len(out) < count:
+    dmin2 = (2 * radius + 1) ** 2
+    while m < count:
         if k > 10000 * count:
             raise ValueError("no room for the discs")
         r = uniform(seed, 2, offset=2 * k)
         k += 1
-        cx, cy = min(int(r[0] * nx), nx - 1), min(int(r[1] * ny), ny - 1)
-        ok = True
-        for ox, oy in out:
-            dx, dy = abs(cx - ox), abs(cy - oy)
-            dx, dy = min(dx, nx - dx), min(dy, ny - dy)
-            if dx * dx + dy * dy < (2 * radius + 1) ** 2:
-                ok = False
-                break
-        if ok:
-            out.append((cx, cy))
-    return out
+        x, y = min(int(r[0] * nx), nx - 1), min(int(r[1] * ny), ny - 1)
+        if m:
+            dx = np.abs(cx[:m] - x)
+            dy = np.abs(cy[:m] - y)
+            dx = np.minimum(dx, nx - dx)
+            dy = np.minimum(dy, ny - dy)
+            if np.any(dx * dx + dy * dy < dmin2):
+                continue
+        cx[m], cy[m] = x, y
+        m += 1
+    return list(zip(cx.tolist(), cy.tolist()))
 
 
 def disc_mask(nx: int, ny: int, centres, radius: float) -> np.ndarray:
     """Solid mask (ny, nx) of discs: cell (x, y) is solid when its periodic
     distance to a centre is at most the radius."""
-    ys, xs = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
     solid = np.zeros((ny, nx), dtype=bool)
+    R = int(np.floor(radius))
+    oy, ox = np.meshgrid(np.arange(-R, R + 1), np.arange(-R, R + 1), indexing="ij")
+    inside = ox * ox + oy * oy <= radius * radius
+    oy, ox = oy[inside], ox[inside]
     for cx, cy in centres:
-        dx = np.abs(xs - cx)
-        dy = np.abs(ys - cy)
-        dx = np.minimum(dx, nx - dx)
-        dy = np.minimum(dy, ny - dy)
-        solid |= dx * dx + dy * dy <= radius * radius
+        solid[(cy + oy) % ny, (cx + ox) % nx] = True
     return solid
 
 

@@ -98,6 +98,8 @@ def _load():
         "lbm_surrogate_load": (C.c_int, [V, V]),
         "lbm_surrogate_stats": (C.c_int, [V, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "lbm_surrogate_engine": (C.c_int, [V, C.c_int32]),
+        "lbm_set_obstacles": (C.c_int, [V, C.c_int32, V, C.c_int32]),
+        "lbm_set_force": (C.c_int, [V, C.c_int32, C.c_double, C.c_double]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -111,7 +113,8 @@ EXPORTS = ("lbm_create", "lbm_init_riemann", "lbm_step", "lbm_moments", "lbm_get
            "lbm_set_populations", "lbm_destroy", "lbm_last_error", "lbm_launch_count",
            "lbm_conservation_sums_static", "lbm_set_tiling", "lbm_get_tiling", "lbm_autotune",
            "lbm_surrogate_targets", "lbm_surrogate_loss_grad", "lbm_surrogate_train", "lbm_surrogate_eval",
-           "lbm_surrogate_load", "lbm_surrogate_stats", "lbm_surrogate_engine")
+           "lbm_surrogate_load", "lbm_surrogate_stats", "lbm_surrogate_engine", "lbm_set_obstacles",
+           "lbm_set_force")
 LBM_SURROGATE_FP32_PIPE, LBM_SURROGATE_TENSOR_CORES = 0, 1
 NPARAM = 4482
 
@@ -198,6 +201,27 @@ def lbm_get_populations(ctx, problem: int, f, on_device=False):
 
 def lbm_set_populations(ctx, problem: int, f, on_device=False):
     _check(LIB.lbm_set_populations(ctx, int(problem), _ptr(f), 1 if on_device else 0), ctx)
+
+
+def lbm_set_obstacles(ctx, problem: int, solid=None, on_device=False):
+    """solid: (ny, nx) mask (NumPy bool / uint8, or a contiguous uint8 / bool
+    device tensor with on_device=True); None removes the obstacles."""
+    keep = None
+    if solid is None:
+        ptr = None
+    elif isinstance(solid, np.ndarray):
+        keep = np.ascontiguousarray(solid, dtype=np.uint8)
+        ptr = keep.ctypes.data
+    else:
+        if not solid.is_contiguous() or solid.element_size() != 1:
+            raise ValueError("device masks must be contiguous 1-byte tensors")
+        ptr = solid.data_ptr()
+    _check(LIB.lbm_set_obstacles(ctx, int(problem), ptr, 1 if on_device else 0), ctx)
+    del keep
+
+
+def lbm_set_force(ctx, problem: int, fx: float, fy: float = 0.0):
+    _check(LIB.lbm_set_force(ctx, int(problem), float(fx), float(fy)), ctx)
 
 
 def lbm_destroy(ctx):
@@ -360,6 +384,12 @@ class Lattice:
         f = np.empty((self.q, p.ny, p.nx))
         lbm_get_populations(self.ctx, i, f)
         return f
+
+    def set_obstacles(self, solid, i: int = 0):
+        lbm_set_obstacles(self.ctx, i, solid)
+
+    def set_force(self, fx: float, fy: float = 0.0, i: int = 0):
+        lbm_set_force(self.ctx, i, fx, fy)
 
     def set_populations(self, f: np.ndarray, i: int = 0):
         lbm_set_populations(self.ctx, i, np.ascontiguousarray(f, dtype=np.float64))
