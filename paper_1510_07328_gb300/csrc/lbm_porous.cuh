@@ -123,8 +123,40 @@ __device__ __forceinline__ void relax_force_store_dev(const ProbDev& P, const fl
   for (int a = 0; a < 9; ++a) fout[a * plane + off] = Dev<T>::st(fmaf(w, ge[a] - g[a], g[a]) + gf[a]);
 }
 
+// True when the tile (kTileX cells from x0, rows y0 .. y1 - 1) and its halo of
+// one cell hold no solid cell; every thread of the CTA takes part.  Each
+// thread scans its column over rows y0 - 1 .. y1, the first and last thread
+// also the halo columns left of the first cell and right of the last one
+// (wrapped where periodic).
+__device__ __forceinline__ bool tile_clean(const ProbDev& P, int x0, int y0, int y1) {
+  bool any = false;
+  if (P.solid != nullptr) {
+    const int t = (int)threadIdx.x;
+    auto col = [&](int x) {
+      if (x < 0 || x >= P.nx) {
+        if (P.bc_x != BC_PERIODIC) return;
+        x = (x + P.nx) % P.nx;
+      }
+      for (int y = y0 - 1; y <= y1; ++y) {
+        int yy = y;
+        if (yy < 0 || yy >= P.ny) {
+          if (P.bc_y != BC_PERIODIC) continue;
+          yy = (yy + P.ny) % P.ny;
+        }
+        any = any || P.solid[P.base + (int64_t)yy * P.pitch + x] != 0;
+      }
+    };
+    if (x0 + t < P.nx) col(x0 + t);
+    if (t == 0) col(x0 - 1);
+    if (t == kTileX - 1) col(min(x0 + kTileX, P.nx));  // right of the tile's last cell
+  }
+  return __syncthreads_or(any) == 0;
+}
+
 // One CTA per tile of 128 cells x TY rows (PERSIST: a smaller grid walks the
-// tiles).  T = double: FP64 populations; float / bf16: deviations.
+// tiles).  T = double: FP64 populations; float / bf16: deviations.  Tiles
+// without solid cells in reach take the pull without mask checks (for FP32 /
+// BF16 the branch-free interior gather).
 template <class T, int STAT, int TY, bool PERSIST>
 __global__ void __launch_bounds__(kTileX) stream_collide_porous(const T* __restrict__ fin, T* __restrict__ fout,
                                                                 const ProbDev* __restrict__ probs, int nprob,
@@ -137,19 +169,26 @@ __global__ void __launch_bounds__(kTileX) stream_collide_porous(const T* __restr
     const ProbDev& P = probs[p];
     const int lt = tile - (int)P.tile_begin;
     const int ty = lt / P.tiles_x;
-    const int x = (lt - ty * P.tiles_x) * kTileX + (int)threadIdx.x;
+    const int x0 = (lt - ty * P.tiles_x) * kTileX;
+    const int x = x0 + (int)threadIdx.x;
+    const int y0 = ty * TY, y1 = min(y0 + TY, P.ny);
+    const bool clean = tile_clean(P, x0, y0, y1);
+    const bool xin = x0 >= 1 && x0 + kTileX <= P.nx - 1;
     if (x < P.nx) {
-      const int y1 = min(ty * TY + TY, P.ny);
 #pragma unroll 1
-      for (int y = ty * TY; y < y1; ++y) {
+      for (int y = y0; y < y1; ++y) {
         const int64_t c = P.base + (int64_t)y * P.pitch + x;
-        if (is_solid(P, c)) continue;
-        T v[9];
-        pull9_obst(fin, plane, P, x, y, v);
+        if (!clean && is_solid(P, c)) continue;
         if constexpr (Stor<T>::dev) {
           float g[9];
+          if (clean) {
+            gather_dev(fin, plane, P, x, y, xin, g);
+          } else {
+            T v[9];
+            pull9_obst(fin, plane, P, x, y, v);
 #pragma unroll
-          for (int a = 0; a < 9; ++a) g[a] = Dev<T>::ld(v[a]);
+            for (int a = 0; a < 9; ++a) g[a] = Dev<T>::ld(v[a]);
+          }
           const CellMom m = dev_moments(P, g);
           float J2, J4;
           if (STAT == STAT_FD) {
@@ -162,6 +201,9 @@ __global__ void __launch_bounds__(kTileX) stream_collide_porous(const T* __restr
           }
           relax_force_store_dev<T, STAT>(P, g, m, J2, J4, fout, plane, (int)c);
         } else {
+          T v[9];
+          if (clean) pull9(fin, plane, pull_index(P, x, y), x, v);
+          else pull9_obst(fin, plane, P, x, y, v);
           collide_force_f64<STAT>(P, v, fout, plane, c, L, Lf);
         }
       }

@@ -29,9 +29,11 @@ def L():
     return lbm
 
 
-def case(nx, ny, seed, stat, bc_x="periodic"):
+def case(nx, ny, seed, stat, bc_x="periodic", centres=None, radius=4):
     p = inputs.random_field(nx, ny, seed, tau=0.8, bc_x=bc_x, t_lo=0.3, t_hi=0.6, u_max=0.05)
-    solid = inputs.disc_mask(nx, ny, inputs.disc_centres(nx, ny, 3, 4, seed), 4)
+    if centres is None:
+        centres = inputs.disc_centres(nx, ny, 3, radius, seed)
+    solid = inputs.disc_mask(nx, ny, centres, radius)
     f = inputs.perturb_populations(olbm.init_equilibrium(p.n, p.ux, p.uy, p.t, stat), seed + 1, 0.01)
     return p, solid, f
 
@@ -86,6 +88,25 @@ def test_step_parity_reduced(L, prec, stat):
         f = porous.step(f, solid, p.tau, stat, FORCE, p.bc_x, p.bc_y)
         tol = 8 * U_STORE[prec] * max(g_in, np.abs(f - W)[:, fl].max()) + 4e-6 * np.abs(f).max()
         assert np.abs(got[:, fl] - f[:, fl]).max() <= tol
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_obstacle_reached_only_through_a_tile_halo(L, prec):
+    """A single disc over x = 0..2, seen by the ragged last tile of a periodic
+    150-wide lattice only through the wrapped halo column, and split by a
+    tile-row boundary (rows 3 | 4)."""
+    p, solid, f = case(150, 24, 35, "mb", centres=[(1, 4)], radius=1.5)
+    lat = L.Lattice([p], stat="mb", prec=prec, n_ref=1.0, t_ref=0.05)
+    lat.set_obstacles(solid)
+    lat.set_force(*FORCE)
+    fl = ~solid
+    ref = porous.run(f, solid, p.tau, "mb", FORCE, 3)
+    lat.set_populations(f)
+    lat.step(3)
+    got = lat.populations(0)
+    tol = 3e-13 if prec == "f64" else 1.5e-5
+    assert np.abs(got[:, fl] - ref[:, fl]).max() <= tol * np.abs(ref).max()
     lat.close()
 
 
