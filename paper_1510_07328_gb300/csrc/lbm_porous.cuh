@@ -129,7 +129,7 @@ __device__ __forceinline__ void relax_force_store_dev(const ProbDev& P, const fl
 // also the halo columns left of the first cell and right of the last one
 // (wrapped where periodic).
 __device__ __forceinline__ bool tile_clean(const ProbDev& P, int x0, int y0, int y1) {
-  bool any = false;
+  unsigned any = 0;  // OR of the mask bytes: independent loads, no short circuit
   if (P.solid != nullptr) {
     const int t = (int)threadIdx.x;
     auto col = [&](int x) {
@@ -143,22 +143,23 @@ __device__ __forceinline__ bool tile_clean(const ProbDev& P, int x0, int y0, int
           if (P.bc_y != BC_PERIODIC) continue;
           yy = (yy + P.ny) % P.ny;
         }
-        any = any || P.solid[P.base + (int64_t)yy * P.pitch + x] != 0;
+        any |= P.solid[P.base + (int64_t)yy * P.pitch + x];
       }
     };
     if (x0 + t < P.nx) col(x0 + t);
     if (t == 0) col(x0 - 1);
     if (t == kTileX - 1) col(min(x0 + kTileX, P.nx));  // right of the tile's last cell
   }
-  return __syncthreads_or(any) == 0;
+  return __syncthreads_or(any != 0) == 0;
 }
 
 // One CTA per tile of 128 cells x TY rows (PERSIST: a smaller grid walks the
-// tiles).  T = double: FP64 populations; float / bf16: deviations.  Tiles
-// without solid cells in reach take the pull without mask checks (for FP32 /
-// BF16 the branch-free interior gather).
+// tiles).  T = double: FP64 populations; float / bf16: deviations, with the
+// next row's loads issued before the current row's collision.  Tiles without
+// solid cells in reach take the pull without mask checks (for FP32 / BF16 the
+// branch-free interior gather).
 template <class T, int STAT, int TY, bool PERSIST>
-__global__ void __launch_bounds__(kTileX) stream_collide_porous(const T* __restrict__ fin, T* __restrict__ fout,
+__global__ void __launch_bounds__(kTileX, sizeof(T) == 8 ? 4 : 6) stream_collide_porous(const T* __restrict__ fin, T* __restrict__ fout,
                                                                 const ProbDev* __restrict__ probs, int nprob,
                                                                 int ntiles, int64_t plane, InvLimits L,
                                                                 InvLimitsF Lf) {
@@ -175,20 +176,31 @@ __global__ void __launch_bounds__(kTileX) stream_collide_porous(const T* __restr
     const bool clean = tile_clean(P, x0, y0, y1);
     const bool xin = x0 >= 1 && x0 + kTileX <= P.nx - 1;
     if (x < P.nx) {
-#pragma unroll 1
-      for (int y = y0; y < y1; ++y) {
-        const int64_t c = P.base + (int64_t)y * P.pitch + x;
-        if (!clean && is_solid(P, c)) continue;
-        if constexpr (Stor<T>::dev) {
-          float g[9];
+      if constexpr (Stor<T>::dev) {
+        // pulled deviations of row y into g; false for a solid cell
+        auto load = [&](int y, float g[9]) -> bool {
           if (clean) {
             gather_dev(fin, plane, P, x, y, xin, g);
-          } else {
-            T v[9];
-            pull9_obst(fin, plane, P, x, y, v);
-#pragma unroll
-            for (int a = 0; a < 9; ++a) g[a] = Dev<T>::ld(v[a]);
+            return true;
           }
+          if (is_solid(P, P.base + (int64_t)y * P.pitch + x)) return false;
+          T v[9];
+          pull9_obst(fin, plane, P, x, y, v);
+#pragma unroll
+          for (int a = 0; a < 9; ++a) g[a] = Dev<T>::ld(v[a]);
+          return true;
+        };
+        // the next row's loads are issued before the current row's collision
+        float gn[9];
+        bool fn = load(y0, gn);
+#pragma unroll 1
+        for (int y = y0; y < y1; ++y) {
+          float g[9];
+#pragma unroll
+          for (int a = 0; a < 9; ++a) g[a] = gn[a];
+          const bool fluid = fn;
+          if (y + 1 < y1) fn = load(y + 1, gn);
+          if (!fluid) continue;
           const CellMom m = dev_moments(P, g);
           float J2, J4;
           if (STAT == STAT_FD) {
@@ -199,8 +211,13 @@ __global__ void __launch_bounds__(kTileX) stream_collide_porous(const T* __restr
             J2 = (float)FixedJ<STAT>::j2;
             J4 = (float)FixedJ<STAT>::j4;
           }
-          relax_force_store_dev<T, STAT>(P, g, m, J2, J4, fout, plane, (int)c);
-        } else {
+          relax_force_store_dev<T, STAT>(P, g, m, J2, J4, fout, plane, (int)(P.base + (int64_t)y * P.pitch + x));
+        }
+      } else {
+#pragma unroll 1
+        for (int y = y0; y < y1; ++y) {
+          const int64_t c = P.base + (int64_t)y * P.pitch + x;
+          if (!clean && is_solid(P, c)) continue;
           T v[9];
           if (clean) pull9(fin, plane, pull_index(P, x, y), x, v);
           else pull9_obst(fin, plane, P, x, y, v);
