@@ -149,11 +149,11 @@ constexpr int kTcSpin = 1 << 22;
 // chains in flight) need 128 TMEM columns, 74 KB of shared memory and about
 // 170 registers per thread, leaving 3 CTAs per SM; one row per round leaves 5
 // and measured 12 % faster on the 4096^2 lattice.
-__host__ __device__ constexpr int tc_rows(int TY) { return TY > 0 ? 1 : 1; }
+__host__ __device__ constexpr int tc_rows(int /*TY*/) { return 1; }
 // Dynamic shared memory of the kernel, in this order: the network's operands;
 // per round row the input block (128 x 16 FP16) and the hidden activations
 // (128 x 64 FP16); two stages of pulled populations (per row 9 x 128 words).
-__host__ __device__ constexpr int tc_smem_x(int R) { return kTcBytes + 0 * R; }
+__host__ __device__ constexpr int tc_smem_x(int /*R*/) { return kTcBytes; }
 __host__ __device__ constexpr int tc_smem_a(int R) { return tc_smem_x(R) + R * kTileX * 16 * 2; }
 __host__ __device__ constexpr int tc_smem_g(int R) { return tc_smem_a(R) + R * kTileX * kH * 2; }
 __host__ __device__ constexpr int tc_smem(int R) { return tc_smem_g(R) + 2 * R * 9 * kTileX * 4; }
