@@ -291,12 +291,38 @@ def oracle_sample_mlups(L: int, tau: float, seconds: float, window: int = 48):
     return window * window * steps / el / 1e6, steps, window, el
 
 
-def run_reference(a, world, rank):
-    if rank != 0:
-        return
-    from oracle import lbm as olbm
+def oracle_workload(a):
+    """A bounded sample of the workload for the CPU oracle: (step, state, cells,
+    description).  Windows wrap periodically in place of the rest of the
+    lattice."""
     from paper_1510_07328_gb300 import inputs
 
+    if a.workload == "d1v3":
+        from oracle import lbm1d
+
+        w = min(1 << 18, a.cells1d)
+        xs = np.arange(a.cells1d // 2 - w // 2, a.cells1d // 2 + w // 2)
+        n = np.where((xs > a.cells1d / 4) & (xs < 3 * a.cells1d / 4), 1.0, 0.85)
+        f = lbm1d.init_equilibrium(n, np.zeros(w), a.stat)
+        return (lambda f: lbm1d.step(f, 0.58, a.stat)), f, w, f"{w} cells of the d1v3 lattice around x = L/2"
+    from oracle import lbm as olbm
+
+    if a.workload == "porous":
+        from oracle import porous
+
+        w = min(128, a.L)
+        solid = inputs.disc_mask(a.L, a.L, inputs.disc_centres(a.L, a.L, porous_discs(a.L), 3, 13), 3)[:w, :w]
+        z = np.zeros((w, w))
+        f = olbm.init_equilibrium(np.ones((w, w)), z, z, np.full((w, w), 0.5), a.stat)
+        return ((lambda f: porous.step(f, solid, 0.7, a.stat, (1e-6, 0.0))), f, w * w,
+                f"{w}x{w} corner of the porous lattice ({int(solid.sum())} solid cells)")
+    if a.workload == "batched":
+        p = inputs.batched()[0]
+        cols = slice(max(p.nx // 2 - 16, 0), p.nx // 2 + 16)
+        f = olbm.init_equilibrium(p.n[:, cols], p.ux[:, cols], p.uy[:, cols], p.t[:, cols], a.stat)
+        par = olbm.Params(tau=p.tau, stat=a.stat)
+        return ((lambda f: olbm.step(f, par)), f, f.shape[1] * f.shape[2],
+                f"{f.shape[2]} columns around the step of batched problem 0 ({p.ny} rows)")
     window = 32
     t = inputs.smooth_t_field(a.L, rows=slice(a.L // 2 - window // 2, a.L // 2 + window // 2))
     x0 = a.L // 2 - window // 2
@@ -304,17 +330,28 @@ def run_reference(a, world, rank):
     xs = np.arange(x0, x0 + window)
     n = np.where(xs < a.L // 2, 1.0, 0.8)[None, :].repeat(window, 0)
     z = np.zeros_like(n)
-    f = olbm.init_equilibrium(n, z, z, t)
-    p = olbm.Params(tau=a.tau)
-    for _ in range(a.warmup):
-        f = olbm.step(f, p)
-    t0 = time.perf_counter()
-    for _ in range(a.steps):
-        f = olbm.step(f, p)
-    el = time.perf_counter() - t0
-    mlups = window * window * a.steps / el / 1e6
-    cfg = workload_config(a, 1)
-    sample = f"{window}x{window} window of the lattice at x = L/2 (periodic wrap), {a.steps} steps"
+    f = olbm.init_equilibrium(n, z, z, t, a.stat)
+    p = olbm.Params(tau=a.tau, stat=a.stat)
+    return (lambda f: olbm.step(f, p)), f, window * window, f"{window}x{window} window of the lattice at x = L/2"
+
+
+def run_reference(a, world, rank):
+    if rank != 0:
+        return
+    step, f, cells, what = oracle_workload(a)
+    # as in the GPU arm: warm-up steps from the initial state, then the timed
+    # steps (states past a few dozen steps of the low-t workloads may turn
+    # non-finite; the timing stands either way)
+    with np.errstate(invalid="ignore", divide="ignore", over="ignore"):
+        for _ in range(a.warmup):
+            f = step(f)
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            f = step(f)
+        el = time.perf_counter() - t0
+    mlups = cells * a.steps / el / 1e6
+    cfg = workload_config(a, 1, inputs_for_config(a))
+    sample = f"{what} (periodic wrap), {a.steps} steps"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": 0,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": el / a.steps * 1e3, "higher_is_better": True,
@@ -322,6 +359,15 @@ def run_reference(a, world, rank):
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def inputs_for_config(a):
+    """The problem list workload_config needs (the batched workload only)."""
+    if a.workload != "batched":
+        return None
+    from paper_1510_07328_gb300 import inputs
+
+    return inputs.batched()
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -343,8 +389,6 @@ def run_ours(a, world, rank, local):
         dev_fields = None
         lat = lbm.Lattice(probs, stat=a.stat, prec=a.prec, stream=stream.cuda_stream, n_ref=1.2, t_ref=0.05)
     elif a.workload == "porous":
-        if a.stat == "fd":
-            a.stat = "mb"  # the closure that is stable at tau = 0.7 around obstacles
         centres = inputs.disc_centres(a.L, a.L, porous_discs(a.L), 3, 13)
         solid = inputs.disc_mask(a.L, a.L, centres, 3)
         prob = inputs.Problem(a.L, a.L, 0.7, "periodic", "periodic", np.ones((a.L, a.L)), np.zeros((a.L, a.L)),
@@ -356,8 +400,6 @@ def run_ours(a, world, rank, local):
         lat.set_obstacles(solid)
         lat.set_force(1e-6, 0.0)
     elif a.workload == "d1v3":
-        if a.stat == "fd":
-            a.stat = "t0"  # d1v3 has no finite-temperature closure
         n1 = a.cells1d
         xs = np.arange(n1)
         n = np.where((xs > n1 / 4) & (xs < 3 * n1 / 4), 1.0, 0.85)[None, :]
@@ -564,8 +606,19 @@ def extras(a, prob, dev_fields, lbm, torch, stream, value, net=None):
     return res
 
 
+def settle_closure(a):
+    """The closure a workload runs with when the FD default does not apply:
+    d1v3 has no finite-temperature closure (theta = 0 instead), and around
+    obstacles at tau = 0.7 the Maxwell-Boltzmann closure is the stable one."""
+    if a.stat == "fd" and a.workload == "d1v3":
+        a.stat = "t0"
+    if a.stat == "fd" and a.workload == "porous":
+        a.stat = "mb"
+
+
 def main():
     a = parse()
+    settle_closure(a)
     world, rank, local = dist_setup(a)
     if a.impl == "reference":
         run_reference(a, world, rank)
