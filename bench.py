@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--inv", default="exact", choices=["exact", "surrogate"],
                     help="per-cell FD inversion: exact, or the learned network (trained first, on 1e6 pairs)")
     ap.add_argument("--train-epochs", type=int, default=32)
+    ap.add_argument("--engine", default="tensor", choices=["tensor", "mma", "fp32"],
+                    help="where the learned inversion's network runs: tcgen05 MMAs over 128-cell tile rows, "
+                         "warp-level MMAs with activations in registers, or the FP32 pipe")
     ap.add_argument("--tau", type=float, default=0.8)
     ap.add_argument("--stat", default="fd", choices=["fd", "t0", "mb"],
                     help="closure: fd (per-cell inversion), t0 (theta = 0), mb (Hermite limit)")
@@ -129,7 +132,9 @@ def workload_config(a, world, probs=None, tiling=None):
                     "mb": "d2v9 K=3 LBGK, Maxwell-Boltzmann limit (J = 1)"}[a.stat],
         "storage": {"f32": "FP32 deviations g = f - W_ref", "bf16": "BF16 deviations", "f64": "FP64 f"}[a.prec],
         "inversion": "exact (closed-form degenerate root, tail passes, Newton)" if a.inv == "exact"
-        else "learned network 2-64-64-2 + one Newton polish + residual check, exact fallback",
+        else "learned network 2-64-64-2 (%s) + one third-order polish + residual check, exact fallback"
+        % {"tensor": "tcgen05 MMAs over 128-cell tile rows", "mma": "warp-level MMAs, activations in registers",
+           "fp32": "FP32 pipe"}[a.engine],
         "tau": a.tau,
         "t_range": [0.01, 0.2],
         "density_step": [1.0, 0.8],
@@ -235,7 +240,8 @@ _EXACT_SRC = ("lbm_kernels.cuh", "fd_device.cuh", "fd_device_f32.cuh", "lbm_dev3
 KERNEL_SOURCES = {
     "stream_collide_dev": _EXACT_SRC + ("step_f32.cu", "step_bf16.cu"),
     "stream_collide_f64": ("lbm_kernels.cuh", "fd_device.cuh", "fd_device_f32.cuh", "launch.h", "step_f64.cu"),
-    "stream_collide_surr": _EXACT_SRC + ("surrogate.cuh", "tc_sm100.cuh", "lbm_surr.cuh", "step_surr.cu"),
+    "stream_collide_surr": _EXACT_SRC + ("surrogate.cuh", "tc_sm100.cuh", "lbm_surr.cuh", "lbm_surr_mma.cuh",
+                                         "step_surr.cu"),
     "stream_collide_porous": _EXACT_SRC + ("lbm_porous.cuh", "step_porous.cu"),
     "stream_collide_d1": ("lbm_kernels.cuh", "fd_device.cuh", "fd_device_f32.cuh", "launch.h", "lbm_d1.cuh",
                           "step_d1.cu"),
@@ -244,7 +250,7 @@ KERNEL_SOURCES = {
 
 def kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES[kernel.split("<")[0].replace("_tc", "")]:
+    for f in KERNEL_SOURCES[kernel.split("<")[0].replace("_tc", "").replace("_mma", "")]:
         h.update(open(os.path.join(ROOT, "paper_1510_07328_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -429,7 +435,7 @@ def run_ours(a, world, rank, local):
         surrogate = {"train": rep, "pairs": 1_000_000, "epochs": a.train_epochs, "batch": 1024}
         lat.close()
         lat = lbm.Lattice(probs, stat="fd", prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05,
-                          inv="surrogate", surrogate=net)
+                          inv="surrogate", surrogate=net, engine=a.engine)
     with torch.cuda.stream(stream):
         lat.init(fields_on_device=dev_fields)
         lat.step(a.warmup)
@@ -493,7 +499,8 @@ def run_ours(a, world, rank, local):
     kname = {"f32": "stream_collide_dev<float,%s>", "bf16": "stream_collide_dev<bf16,%s>",
              "f64": "stream_collide_f64<%s>"}[a.prec] % a.stat.upper()
     if a.inv == "surrogate":
-        kname = {"f32": "stream_collide_surr_tc<float>", "bf16": "stream_collide_surr_tc<bf16>"}[a.prec]
+        kname = {"tensor": "stream_collide_surr_tc<%s>", "mma": "stream_collide_surr_mma<%s>",
+                 "fp32": "stream_collide_surr<%s>"}[a.engine] % {"f32": "float", "bf16": "bf16"}[a.prec]
     if a.workload == "porous":
         kname = "stream_collide_porous<%s,%s>" % ({"f32": "float", "bf16": "bf16", "f64": "double"}[a.prec],
                                                   a.stat.upper())
@@ -543,8 +550,9 @@ def extras(a, prob, dev_fields, lbm, torch, stream, value, net=None):
     res["fp64_gpu"] = {"value": v64, "unit": "MLUPS", "steps": k64}
     res["speedup_vs_fp64"] = value / v64
     # field error of the reduced-precision path against FP64 after N steps
+    eng = a.engine if a.inv == "surrogate" else None
     lr = lbm.Lattice([prob], stat="fd", prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05,
-                     inv=a.inv, surrogate=net)
+                     inv=a.inv, surrogate=net, engine=eng)
     with torch.cuda.stream(stream):
         lr.init(fields_on_device=dev_fields)
         lat64.init(fields_on_device=dev_fields)
@@ -586,7 +594,7 @@ def extras(a, prob, dev_fields, lbm, torch, stream, value, net=None):
         host[k][...] = getattr(prob, k)
     outs = {k: pinned() for k in ("n", "ux", "uy", "T")}
     le = lbm.Lattice([prob], stat="fd", prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05,
-                     inv=a.inv, surrogate=net)
+                     inv=a.inv, surrogate=net, engine=eng)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     lbm.lbm_init_riemann(le.ctx, 0, "field", fields=host)  # host fields -> device inside the call

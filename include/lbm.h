@@ -291,15 +291,21 @@ lbm_status lbm_surrogate_eval(const float* params, const double* n, const double
  * context, NULL, non-finite values), LBM_ENOMEM. */
 lbm_status lbm_surrogate_load(lbm_ctx* ctx, const float* params);
 
-/* Where the network runs: its three layers on the tensor cores (tcgen05 MMA
- * over a tile row of 128 cells, FP16 operands with the inputs, layer-1 and
- * layer-3 weights and all biases split into FP16 hi + lo parts, FP32
- * accumulation in tensor memory, SiLU in packed FP16; the default) or per
- * cell on the FP32 pipe (FP32 throughout).  Either way the network's x = mu/T
- * is polished by one third-order step on J_2(x) = J_2 (one evaluation of
- * f_0..f_4) and accepted when the first-order step is below 2.5e-2 max(|x|, 1).
- * Drops captured graphs. */
-enum { LBM_SURROGATE_FP32_PIPE = 0, LBM_SURROGATE_TENSOR_CORES = 1 };
+/* Where the network runs:
+ *  - LBM_SURROGATE_TENSOR_CORES (the default): its three layers as tcgen05
+ *    MMAs over a tile row of 128 cells, FP16 operands with the inputs,
+ *    layer-1 and layer-3 weights and all biases split into FP16 hi + lo
+ *    parts, FP32 accumulation in tensor memory, SiLU in packed FP16;
+ *  - LBM_SURROGATE_WARP_MMA: the same network, operands and splits, each warp
+ *    on its own 32 cells with warp-level MMAs (mma.sync m16n8k8 / m16n8k16),
+ *    FP32 accumulators in registers (layer-2 and layer-3 biases as FP32
+ *    initial values), activations passed from layer to layer in registers;
+ *  - LBM_SURROGATE_FP32_PIPE: per cell on the FP32 pipe (FP32 throughout).
+ * In every case the network's x = mu/T is polished by one third-order step on
+ * J_2(x) = J_2 (one evaluation of f_0..f_4) and accepted when the first-order
+ * step is below 2.5e-2 max(|x|, 1).  Drops captured graphs.  Errors:
+ * LBM_EINVAL (NULL context, unknown engine). */
+enum { LBM_SURROGATE_FP32_PIPE = 0, LBM_SURROGATE_TENSOR_CORES = 1, LBM_SURROGATE_WARP_MMA = 2 };
 lbm_status lbm_surrogate_engine(lbm_ctx* ctx, int32_t engine);
 
 /* Cells that went through the network (finite J_2 inside the clamp

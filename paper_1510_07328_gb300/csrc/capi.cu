@@ -134,8 +134,10 @@ struct lbm_ctx {
   MlpParams* surr = nullptr;               // host copy of the network (learned inversion)
   unsigned long long* surr_count = nullptr;  // device: fallbacks, evaluations, tensor-core timeouts
   void* wtc = nullptr;                       // device: the network's FP16 tensor-core operands (kTcBytes)
+  void* wmm = nullptr;                       // device: the network's warp-MMA fragments (kMmBytes)
   int surr_engine = LBM_SURROGATE_TENSOR_CORES;
   int64_t tc_grid[9] = {};  // persistent grid of the tensor-core kernel per rows per tile: SMs x resident CTAs
+  int64_t mm_grid[9] = {};  // the same for the warp-MMA kernel
 };
 
 namespace {
@@ -176,14 +178,18 @@ void launch_step(lbm_ctx* c, const void* in, void* out, cudaStream_t s) {
     return;
   }
   if (c->inv == LBM_INV_SURROGATE) {
-    const bool tcore = c->surr_engine == LBM_SURROGATE_TENSOR_CORES;
-    // the tensor-core kernel stages the network once per CTA: persistent grid
-    const unsigned gtc = (unsigned)std::min<int64_t>(c->ctas > 0 ? c->ctas : c->tc_grid[c->rows], c->ntiles);
-    if (c->prec == LBM_F32_DEV) {
-      if (tcore) launch_step_surr_tc_f32(c->rows, gtc, s, a, c->surr_count, c->wtc);
-      else launch_step_surr_f32(c->rows, grid, s, a, c->surr_count, *c->surr);
+    const bool f32 = c->prec == LBM_F32_DEV;
+    // the tensor-core kernels stage the network once per CTA: persistent grid
+    if (c->surr_engine == LBM_SURROGATE_TENSOR_CORES) {
+      const unsigned g = (unsigned)std::min<int64_t>(c->ctas > 0 ? c->ctas : c->tc_grid[c->rows], c->ntiles);
+      if (f32) launch_step_surr_tc_f32(c->rows, g, s, a, c->surr_count, c->wtc);
+      else launch_step_surr_tc_bf16(c->rows, g, s, a, c->surr_count, c->wtc);
+    } else if (c->surr_engine == LBM_SURROGATE_WARP_MMA) {
+      const unsigned g = (unsigned)std::min<int64_t>(c->ctas > 0 ? c->ctas : c->mm_grid[c->rows], c->ntiles);
+      if (f32) launch_step_surr_mma_f32(c->rows, g, s, a, c->surr_count, c->wmm);
+      else launch_step_surr_mma_bf16(c->rows, g, s, a, c->surr_count, c->wmm);
     } else {
-      if (tcore) launch_step_surr_tc_bf16(c->rows, gtc, s, a, c->surr_count, c->wtc);
+      if (f32) launch_step_surr_f32(c->rows, grid, s, a, c->surr_count, *c->surr);
       else launch_step_surr_bf16(c->rows, grid, s, a, c->surr_count, *c->surr);
     }
     return;
@@ -348,14 +354,18 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
     e = cudaMalloc(&ctx->surr_count, 3 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->surr_count, 0, 3 * sizeof(unsigned long long), ctx->stream);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->wtc, kTcBytes);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->wmm, kMmBytes);
     if (e == cudaSuccess) {
       int dev = 0, sms = 0;
       e = cudaGetDevice(&dev);
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       for (int rows : {1, 2, 4, 8}) {
-        const int per_sm = e == cudaSuccess ? prepare_surr_tc(p->prec == LBM_BF16_DEV, rows) : 0;
-        if (e == cudaSuccess && per_sm <= 0) e = cudaErrorInvalidConfiguration;
+        const bool bf16 = p->prec == LBM_BF16_DEV;
+        const int per_sm = e == cudaSuccess ? prepare_surr_tc(bf16, rows) : 0;
+        const int per_sm_mm = e == cudaSuccess ? prepare_surr_mma(bf16, rows) : 0;
+        if (e == cudaSuccess && (per_sm <= 0 || per_sm_mm <= 0)) e = cudaErrorInvalidConfiguration;
         ctx->tc_grid[rows] = (int64_t)per_sm * sms;
+        ctx->mm_grid[rows] = (int64_t)per_sm_mm * sms;
       }
     }
   }
@@ -541,6 +551,62 @@ std::vector<__half> pack_tc_operands(const float* p) {
   return out;
 }
 
+// The network's warp-MMA fragments (layout in surrogate.cuh), as 32-bit words:
+// two FP16 values per word, the lower k in the low half.
+std::vector<uint32_t> pack_mma_operands(const float* p) {
+  std::vector<uint32_t> out(kMmBytes / 4, 0u);
+  auto h16 = [](float v) { const __half h = __float2half_rn(v); return (uint32_t)*reinterpret_cast<const uint16_t*>(&h); };
+  auto pair = [&](float lo_k, float hi_k) { return h16(lo_k) | (h16(hi_k) << 16); };
+  auto hi = [](float v) { return __half2float(__float2half_rn(v)); };
+  auto f32 = [](float v) { uint32_t u; std::memcpy(&u, &v, 4); return u; };
+  // layer-1 rows: the 8 features of hidden unit j (W1/2 and b1/2 split hi/lo)
+  float w1[kH][8];
+  for (int j = 0; j < kH; ++j) {
+    const float wn = 0.5f * p[kOW1 + 2 * j], wl = 0.5f * p[kOW1 + 2 * j + 1], b = 0.5f * p[kOB1 + j];
+    const float row[8] = {hi(wn), hi(wn), wn - hi(wn), hi(wl), hi(wl), wl - hi(wl), hi(b), b - hi(b)};
+    for (int k = 0; k < 8; ++k) w1[j][k] = row[k];
+  }
+  for (int lane = 0; lane < 32; ++lane) {
+    const int g = lane / 4, t = lane % 4;
+    for (int q = 0; q < 4; ++q)
+      for (int h = 0; h < 2; ++h) {
+        const int n = 8 * (2 * q + h) + g;
+        out[(kMmB1 + (q * 32 + lane) * 8) / 4 + h] = pair(w1[n][2 * t], w1[n][2 * t + 1]);
+      }
+    // layer 2: element (k, n) = W2[n][k]/2
+    auto w2 = [&](int k, int n) { return 0.5f * p[kOW2 + kH * n + k]; };
+    for (int c = 0; c < 4; ++c)
+      for (int q = 0; q < 4; ++q)
+        for (int h = 0; h < 2; ++h) {
+          const int n = 8 * (2 * q + h) + g, k = 16 * c + 2 * t;
+          const int w = (kMmB2 + ((c * 4 + q) * 32 + lane) * 16) / 4 + 2 * h;
+          out[w] = pair(w2(k, n), w2(k + 1, n));
+          out[w + 1] = pair(w2(k + 8, n), w2(k + 9, n));
+        }
+    // layer 3: element (k, n) = W3[n][k] for n = 0, 1, as hi and lo parts
+    auto w3 = [&](int k, int n, bool lo) {
+      if (n > 1) return 0.0f;
+      const float v = p[kOW3 + kH * n + k];
+      return lo ? v - hi(v) : hi(v);
+    };
+    for (int c = 0; c < 4; ++c)
+      for (int h = 0; h < 2; ++h) {
+        const int k = 16 * c + 2 * t, w = (kMmB3 + (c * 32 + lane) * 16) / 4 + 2 * h;
+        out[w] = pair(w3(k, g, h == 1), w3(k + 1, g, h == 1));
+        out[w + 1] = pair(w3(k + 8, g, h == 1), w3(k + 9, g, h == 1));
+      }
+  }
+  for (int q = 0; q < 4; ++q)
+    for (int t = 0; t < 4; ++t)
+      for (int h = 0; h < 2; ++h) {
+        const int nt = 2 * q + h;
+        out[(kMmC2 + (q * 4 + t) * 8) / 4 + h] = pair(0.5f * p[kOB2 + 8 * nt + 2 * t], 0.5f * p[kOB2 + 8 * nt + 2 * t + 1]);
+      }
+  out[kMmC3 / 4] = f32(p[kOB3]);
+  out[kMmC3 / 4 + 1] = f32(p[kOB3 + 1]);
+  return out;
+}
+
 }  // namespace
 
 lbm_status lbm_surrogate_load(lbm_ctx* ctx, const float* params) {
@@ -554,7 +620,9 @@ lbm_status lbm_surrogate_load(lbm_ctx* ctx, const float* params) {
   if (!ctx->surr) return fail(ctx, LBM_ENOMEM, "lbm_surrogate_load: host allocation failed");
   std::memcpy(ctx->surr->p, params, sizeof(float) * kNParam);
   const std::vector<__half> wtc = pack_tc_operands(params);
+  const std::vector<uint32_t> wmm = pack_mma_operands(params);
   CK(cudaMemcpyAsync(ctx->wtc, wtc.data(), kTcBytes, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->wmm, wmm.data(), kMmBytes, cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   drop_graphs(ctx);
   return LBM_OK;
@@ -562,7 +630,7 @@ lbm_status lbm_surrogate_load(lbm_ctx* ctx, const float* params) {
 
 lbm_status lbm_surrogate_engine(lbm_ctx* ctx, int32_t engine) {
   if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_surrogate_engine: NULL context");
-  if (engine != LBM_SURROGATE_FP32_PIPE && engine != LBM_SURROGATE_TENSOR_CORES)
+  if (engine != LBM_SURROGATE_FP32_PIPE && engine != LBM_SURROGATE_TENSOR_CORES && engine != LBM_SURROGATE_WARP_MMA)
     return fail(ctx, LBM_EINVAL, "lbm_surrogate_engine: bad engine");
   ctx->surr_engine = engine;
   drop_graphs(ctx);
@@ -820,6 +888,7 @@ lbm_status lbm_destroy(lbm_ctx* ctx) {
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
   if (ctx->surr_count) cudaFree(ctx->surr_count);
   if (ctx->wtc) cudaFree(ctx->wtc);
+  if (ctx->wmm) cudaFree(ctx->wmm);
   if (ctx->mask) cudaFree(ctx->mask);
   delete ctx->surr;
   delete ctx;

@@ -39,6 +39,14 @@ void launch_step_surr_tc_f32(int rows, unsigned grid, cudaStream_t s, const Step
                              unsigned long long* counters, const void* wtc);
 void launch_step_surr_tc_bf16(int rows, unsigned grid, cudaStream_t s, const StepArgs& a,
                               unsigned long long* counters, const void* wtc);
+// the same with the network by warp-level MMAs (mma.sync); wmm: the network's
+// fragments (kMmBytes bytes, 16-byte aligned).  prepare_surr_mma returns the
+// kernels' CTAs resident per SM for `rows` rows per tile (0: error).
+int prepare_surr_mma(bool bf16, int rows);
+void launch_step_surr_mma_f32(int rows, unsigned grid, cudaStream_t s, const StepArgs& a,
+                              unsigned long long* counters, const void* wmm);
+void launch_step_surr_mma_bf16(int rows, unsigned grid, cudaStream_t s, const StepArgs& a,
+                               unsigned long long* counters, const void* wmm);
 // d1v3 (prec 0 FP64, 1 FP32 deviations, 2 BF16 deviations; stat STAT_T0 or
 // STAT_MB): step, initial equilibrium, moments with per-block partial sums,
 // and populations to (get) or from FP64 buffers [3][nx]

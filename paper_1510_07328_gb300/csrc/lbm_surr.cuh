@@ -275,7 +275,10 @@ __global__ void __launch_bounds__(kTileX, tc_rows(TY) == 1 ? 5 : 3)
   const uint32_t tmem = tmem_slot;
   const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
   const uint32_t uA = tc::smem_u32(sA), uX = tc::smem_u32(sX), uW = tc::smem_u32(sW), uG = tc::smem_u32(sG);
-  const uint32_t id64 = tc::idesc_f16_f32(kTileX, kH), id16 = tc::idesc_f16_f32(kTileX, 16);
+  // layers 1 and 2 accumulate in FP16 (their outputs become FP16 operands
+  // anyway; the polish and the residual check absorb the rounding), layer 3
+  // in FP32
+  const uint32_t id64 = tc::idesc_f16_f16(kTileX, kH), id16 = tc::idesc_f16_f32(kTileX, 16);
   constexpr uint32_t kLboA = (kTileX / 8) * 128, kLbo64 = (kH / 8) * 128, kLbo16 = (16 / 8) * 128;
   constexpr uint32_t kBlkX = kTileX * 16 * 2, kBlkA = kTileX * kH * 2, kRowG = 9 * kTileX * 4;
   uint32_t phase = 0, last = 0;
@@ -323,21 +326,19 @@ __global__ void __launch_bounds__(kTileX, tc_rows(TY) == 1 ? 5 : 3)
     __syncthreads();
     tc::fence_after();
   };
-  // SiLU of the TMEM columns of row r (holding z/2) into row tid of sA block r
+  // SiLU of the FP16 TMEM columns of row r (holding z/2) into row tid of sA
+  // block r: the packed load gives the pairs (k, k + 1) the operand stores
   auto act_store = [&](int r) {
+    uint32_t v[32];
+    tc::tmem_ld64_pack16(tl + (uint32_t)(r * kH), v);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      float v[32];
-      tc::tmem_ld32(tl + (uint32_t)(r * kH + 32 * h), v);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        uint4 w;
-        w.x = tc::silu2_half_arg(v[8 * c + 0], v[8 * c + 1]);
-        w.y = tc::silu2_half_arg(v[8 * c + 2], v[8 * c + 3]);
-        w.z = tc::silu2_half_arg(v[8 * c + 4], v[8 * c + 5]);
-        w.w = tc::silu2_half_arg(v[8 * c + 6], v[8 * c + 7]);
-        *reinterpret_cast<uint4*>(sA + r * kBlkA + tc::kmajor_off(tid, 32 * h + 8 * c, kTileX)) = w;
-      }
+    for (int c = 0; c < 8; ++c) {
+      uint4 w;
+      w.x = tc::silu2_packed(v[4 * c + 0]);
+      w.y = tc::silu2_packed(v[4 * c + 1]);
+      w.z = tc::silu2_packed(v[4 * c + 2]);
+      w.w = tc::silu2_packed(v[4 * c + 3]);
+      *reinterpret_cast<uint4*>(sA + r * kBlkA + tc::kmajor_off(tid, 8 * c, kTileX)) = w;
     }
   };
   // round k of this CTA: its problem, tile origin and rows

@@ -3,6 +3,7 @@
 #include <algorithm>
 
 #include "lbm_surr.cuh"
+#include "lbm_surr_mma.cuh"
 
 namespace lbm {
 
@@ -106,6 +107,58 @@ void launch_step_surr_tc_f32(int rows, unsigned grid, cudaStream_t s, const Step
 void launch_step_surr_tc_bf16(int rows, unsigned grid, cudaStream_t s, const StepArgs& a,
                               unsigned long long* counters, const void* wtc) {
   surr_tc_rows<__nv_bfloat16>(rows, grid, s, a, counters, wtc);
+}
+
+template <class T, int TY>
+static void go_surr_mma(unsigned grid, cudaStream_t s, const StepArgs& a, unsigned long long* c, const void* wmm) {
+  const uint4* w = (const uint4*)wmm;
+  if ((int)grid < a.ntiles)
+    stream_collide_surr_mma<T, TY, true><<<grid, kTileX, 0, s>>>((const T*)a.in, (T*)a.out, a.probs, a.nprob,
+                                                                 a.ntiles, a.plane, a.limf, c, w);
+  else
+    stream_collide_surr_mma<T, TY, false><<<grid, kTileX, 0, s>>>((const T*)a.in, (T*)a.out, a.probs, a.nprob,
+                                                                  a.ntiles, a.plane, a.limf, c, w);
+}
+
+template <class T, int TY>
+static int resident_mma() {
+  int n1 = 0, n2 = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, stream_collide_surr_mma<T, TY, true>, kTileX, 0) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, stream_collide_surr_mma<T, TY, false>, kTileX, 0) !=
+          cudaSuccess)
+    return 0;
+  return std::min(n1, n2);
+}
+
+int prepare_surr_mma(bool bf16, int rows) {
+  switch (rows) {
+    case 1: return bf16 ? resident_mma<__nv_bfloat16, 1>() : resident_mma<float, 1>();
+    case 2: return bf16 ? resident_mma<__nv_bfloat16, 2>() : resident_mma<float, 2>();
+    case 8: return bf16 ? resident_mma<__nv_bfloat16, 8>() : resident_mma<float, 8>();
+    default: return bf16 ? resident_mma<__nv_bfloat16, 4>() : resident_mma<float, 4>();
+  }
+}
+
+template <class T>
+static void surr_mma_rows(int rows, unsigned grid, cudaStream_t s, const StepArgs& a, unsigned long long* c,
+                          const void* wmm) {
+  switch (rows) {
+    case 1: go_surr_mma<T, 1>(grid, s, a, c, wmm); break;
+    case 2: go_surr_mma<T, 2>(grid, s, a, c, wmm); break;
+    case 8: go_surr_mma<T, 8>(grid, s, a, c, wmm); break;
+    default: go_surr_mma<T, 4>(grid, s, a, c, wmm); break;
+  }
+}
+
+void launch_step_surr_mma_f32(int rows, unsigned grid, cudaStream_t s, const StepArgs& a,
+                              unsigned long long* counters, const void* wmm) {
+  surr_mma_rows<float>(rows, grid, s, a, counters, wmm);
+}
+
+void launch_step_surr_mma_bf16(int rows, unsigned grid, cudaStream_t s, const StepArgs& a,
+                               unsigned long long* counters, const void* wmm) {
+  surr_mma_rows<__nv_bfloat16>(rows, grid, s, a, counters, wmm);
 }
 
 }  // namespace lbm

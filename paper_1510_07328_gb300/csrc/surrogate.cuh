@@ -57,6 +57,29 @@ __host__ __device__ constexpr int tc_operand_byte(int r, int k, int R) {
   return ((k / 8) * (R / 8) + r / 8) * 128 + (r % 8) * 16 + (k % 8) * 2;
 }
 
+// The network as warp-level MMA fragments (mma.sync m16n8k8 / m16n8k16, FP16
+// operands; FP16 accumulators for layers 1 and 2, FP32 for layer 3), one
+// buffer in the order the lanes read it.
+// Lane l has group g = l/4 and index t = l%4; a B fragment of an 8-column
+// n-tile holds element (k, n = g) for k = 2t, 2t+1 (and 2t+8, 2t+9 when
+// K = 16), packed low element first.  Byte offsets:
+//   kMmB1  [p 0..3][lane] 2 x u32  layer 1 (K = 8), n-tiles 2p and 2p+1: the
+//                                  8-feature rows of kTcB1 (W1/2, b1/2 hi/lo)
+//   kMmB2  [c 0..3][p 0..3][lane] 4 x u32  layer 2 (K = 16 chunk c), n-tiles
+//                                  2p and 2p+1 of W2/2 (element (k, n) =
+//                                  W2[n][k]/2)
+//   kMmC2  [p 0..3][t] 2 x u32     b2/2 for columns 8 nt + 2t, 8 nt + 2t + 1
+//                                  as FP16 pairs, nt = 2p then 2p + 1 (the
+//                                  FP16 accumulators' initial values)
+//   kMmB3  [c 0..3][lane] 4 x u32  layer 3, K = 16 chunk c: the fragment of
+//                                  W3 hi, then of W3 lo (columns 0, 1; the
+//                                  other six zero); both accumulate into the
+//                                  same two columns
+//   kMmC3  2 x f32                 b3
+// The halving makes layers 1 and 2 produce z/2, as for the tcgen05 operands.
+constexpr int kMmB1 = 0, kMmB2 = kMmB1 + 4 * 32 * 8, kMmC2 = kMmB2 + 16 * 32 * 16, kMmB3 = kMmC2 + 4 * 4 * 8,
+              kMmC3 = kMmB3 + 4 * 32 * 16, kMmBytes = kMmC3 + 16;  // 11408
+
 __device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
 // Network output (y_0, y_1) for one cell given n and delta = 3/2 - J_2

@@ -42,6 +42,11 @@ __host__ __device__ constexpr uint32_t idesc_f16_f32(uint32_t M, uint32_t N) {
   return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
+// The same with an FP16 accumulator (D format 0).
+__host__ __device__ constexpr uint32_t idesc_f16_f16(uint32_t M, uint32_t N) {
+  return ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {  // one full warp
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols));
   asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -127,6 +132,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
 }
 
+// 64 consecutive 16-bit columns of this thread's TMEM lane (an FP16
+// accumulator), packed in pairs: r[i] holds columns 2i (low half) and 2i + 1
+// (the .x32 repetition count counts the 32-bit registers written).
+__device__ __forceinline__ void tmem_ld64_pack16(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.pack::16b.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%"
+      "28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // 4 consecutive FP32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
   uint32_t r[4];
@@ -147,6 +168,15 @@ __device__ __forceinline__ __half2 silu2_h(float z0, float z1) {
   asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(*reinterpret_cast<const uint32_t*>(&hz)));
   const __half2 th = *reinterpret_cast<const __half2*>(&t);
   return __hfma2(hz, th, hz);
+}
+
+// SiLU of a packed FP16 pair of halved arguments h = z/2: h + h tanh(h).
+__device__ __forceinline__ uint32_t silu2_packed(uint32_t h) {
+  uint32_t t;
+  asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(h));
+  const __half2 hv = *reinterpret_cast<const __half2*>(&h), tv = *reinterpret_cast<const __half2*>(&t);
+  const __half2 s = __hfma2(hv, tv, hv);
+  return *reinterpret_cast<const uint32_t*>(&s);
 }
 
 // The same from the halved arguments h = z/2 (weights pre-scaled by 1/2):

@@ -115,7 +115,7 @@ EXPORTS = ("lbm_create", "lbm_init_riemann", "lbm_step", "lbm_moments", "lbm_get
            "lbm_surrogate_targets", "lbm_surrogate_loss_grad", "lbm_surrogate_train", "lbm_surrogate_eval",
            "lbm_surrogate_load", "lbm_surrogate_stats", "lbm_surrogate_engine", "lbm_set_obstacles",
            "lbm_set_force")
-LBM_SURROGATE_FP32_PIPE, LBM_SURROGATE_TENSOR_CORES = 0, 1
+LBM_SURROGATE_FP32_PIPE, LBM_SURROGATE_TENSOR_CORES, LBM_SURROGATE_WARP_MMA = 0, 1, 2
 NPARAM = 4482
 
 
@@ -324,10 +324,16 @@ def lbm_surrogate_load(ctx, params):
     _check(LIB.lbm_surrogate_load(ctx, pp), ctx)
 
 
+SURROGATE_ENGINES = {"fp32": LBM_SURROGATE_FP32_PIPE, "tensor": LBM_SURROGATE_TENSOR_CORES,
+                     "mma": LBM_SURROGATE_WARP_MMA}
+
+
 def lbm_surrogate_engine(ctx, engine: str = "tensor"):
-    """'tensor' (tcgen05 hidden layer, default) or 'fp32' (FP32 pipe)."""
-    _check(LIB.lbm_surrogate_engine(ctx, LBM_SURROGATE_TENSOR_CORES if engine == "tensor" else
-                                    LBM_SURROGATE_FP32_PIPE), ctx)
+    """'tensor' (tcgen05 MMAs over 128-cell tile rows, default), 'mma'
+    (warp-level MMAs, activations in registers) or 'fp32' (FP32 pipe)."""
+    if engine not in SURROGATE_ENGINES:
+        raise ValueError(f"unknown surrogate engine {engine!r}")
+    _check(LIB.lbm_surrogate_engine(ctx, SURROGATE_ENGINES[engine]), ctx)
 
 
 def lbm_surrogate_stats(ctx) -> dict:
@@ -352,7 +358,7 @@ class Lattice:
     """One context over a list of problems (``inputs.Problem`` objects)."""
 
     def __init__(self, problems, stat="fd", prec="f64", stream=None, t_ref=None, n_ref=None, inv="exact",
-                 surrogate=None, dim=2):
+                 surrogate=None, dim=2, engine=None):
         self.problems = list(problems)
         self.q = 9 if dim == 2 else 3
         descs = []
@@ -365,6 +371,8 @@ class Lattice:
         self.stat = stat
         if surrogate is not None:
             lbm_surrogate_load(self.ctx, surrogate)
+        if engine is not None:
+            lbm_surrogate_engine(self.ctx, engine)
 
     def init(self, index=None, fields_on_device=None):
         for i, p in enumerate(self.problems):

@@ -86,11 +86,13 @@ def test_eval_matches_oracle_network(L, trained):
     np.testing.assert_allclose(mu_g, mu_o, rtol=2e-5, atol=1e-7)
 
 
+@pytest.mark.parametrize("engine", ["tensor", "mma"])
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
-def test_learned_step_parity(L, trained, prec):
+def test_learned_step_parity(L, trained, prec, engine):
     """The learned step reaches the exact inversion's result (to the FP32
     tolerance of test_gpu_reduced): accepted cells are polished to it, the
-    others fall back."""
+    others fall back.  300 columns: the last tile has one full warp, one with
+    12 cells and two without any."""
     p_net, _ = trained
     prob = inputs.random_field(300, 5, 61, tau=0.7, bc_x="bounceback", t_lo=0.02, t_hi=0.25)
     n_ref, t_ref = 0.95, 0.05
@@ -99,7 +101,7 @@ def test_learned_step_parity(L, trained, prec):
     W = gpoly.weights(2, n_ref, float(fd.j2_of_x(fd.x_of_t(np.array([t_ref])))[0]))[:, None, None]
     f = inputs.perturb_populations(olbm.init_equilibrium(prob.n, prob.ux, prob.uy, prob.t), 71, 0.002)
     par = olbm.Params(tau=prob.tau, bc_x=prob.bc_x, bc_y=prob.bc_y)
-    lat = L.Lattice([prob], prec=prec, inv="surrogate", surrogate=p_net, n_ref=n_ref, t_ref=t_ref)
+    lat = L.Lattice([prob], prec=prec, inv="surrogate", surrogate=p_net, n_ref=n_ref, t_ref=t_ref, engine=engine)
     u = {"f32": 2.0 ** -24, "bf16": 2.0 ** -8}[prec]
     for _ in range(2):
         lat.set_populations(f)
@@ -116,10 +118,48 @@ def test_learned_step_parity(L, trained, prec):
     assert 0 <= st["fallbacks"] <= st["evaluations"]
 
 
+@pytest.mark.parametrize("engine", ["tensor", "mma"])
+def test_learned_step_batched_and_narrow(L, trained, engine):
+    """Several problems in one launch, some narrower than a warp (5 and 20
+    columns) and one with clamped cells (t down to 5e-4: about 40 % of its
+    cells lie beyond the clamp interval, so warps mix network and exact
+    cells), for two steps from the oracle's states, with one tile per CTA and
+    with a persistent grid of 3 CTAs."""
+    p_net, _ = trained
+    probs = [inputs.random_field(20, 7, 81, tau=0.7, t_lo=0.03, t_hi=0.2),
+             inputs.random_field(5, 3, 82, tau=0.9, bc_x="bounceback", t_lo=0.05, t_hi=0.2),
+             inputs.random_field(161, 9, 83, tau=0.6, bc_y="bounceback", t_lo=5e-4, t_hi=0.05, u_max=0.02),
+             inputs.random_field(64, 4, 84, tau=0.8, t_lo=0.02, t_hi=0.3)]
+    n_ref, t_ref = 1.0, 0.05
+    from oracle import fd, gpoly
+
+    W = gpoly.weights(2, n_ref, float(fd.j2_of_x(fd.x_of_t(np.array([t_ref])))[0]))[:, None, None]
+    fs = [inputs.perturb_populations(olbm.init_equilibrium(p.n, p.ux, p.uy, p.t), 90 + i, 0.002)
+          for i, p in enumerate(probs)]
+    for ctas in (0, 3):
+        lat = L.Lattice(probs, prec="f32", inv="surrogate", surrogate=p_net, n_ref=n_ref, t_ref=t_ref, engine=engine)
+        if ctas:
+            L.lbm_set_tiling(lat.ctx, 2, ctas)
+        for i, f in enumerate(fs):
+            lat.set_populations(f, i)
+        lat.step(2)
+        for i, (p, f) in enumerate(zip(probs, fs)):
+            par = olbm.Params(tau=p.tau, bc_x=p.bc_x, bc_y=p.bc_y)
+            ref = olbm.run(f, par, 2)
+            got = lat.populations(i)
+            tol = 2 * (8 * 2.0 ** -24 * max(np.abs(f - W).max(), np.abs(ref - W).max()) + 4e-6 * np.abs(ref).max())
+            assert np.abs(got - ref).max() <= tol, (ctas, i)
+        st = L.lbm_surrogate_stats(lat.ctx)
+        lat.close()
+        cells = sum(p.cells for p in probs)
+        assert 0 < st["evaluations"] < 2 * cells  # the clamped cells skip the network
+
+
 def test_learned_inversion_against_exact_path(L, trained):
     """What the network gains over the method without it: fields after 10
-    steps agree with the exact-inversion path to FP32 accuracy, for the hidden
-    layer on the tensor cores and on the FP32 pipe; the fallback fraction and
+    steps agree with the exact-inversion path to FP32 accuracy, for the
+    network on the tensor cores (tcgen05 and warp-level MMAs) and on the FP32
+    pipe; the fallback fraction and
     the time of each path are printed (the network costs about 4.5 k MAC per
     cell, the exact inversion a few hundred instructions)."""
     import torch
@@ -127,7 +167,8 @@ def test_learned_inversion_against_exact_path(L, trained):
     p_net, _ = trained
     prob = inputs.random_field(512, 128, 62, tau=0.8, u_max=0.01, n_lo=0.95, n_hi=1.05, t_lo=0.03, t_hi=0.2)
     res = {}
-    for name, inv, engine in (("exact", "exact", None), ("fp32", "surrogate", "fp32"), ("tensor", "surrogate", "tensor")):
+    for name, inv, engine in (("exact", "exact", None), ("fp32", "surrogate", "fp32"), ("tensor", "surrogate", "tensor"),
+                              ("mma", "surrogate", "mma")):
         lat = L.Lattice([prob], prec="f32", inv=inv, surrogate=p_net if inv == "surrogate" else None,
                         n_ref=1.0, t_ref=0.1)
         if engine:
@@ -144,7 +185,7 @@ def test_learned_inversion_against_exact_path(L, trained):
         res[name] = (lat.fields(0), e0.elapsed_time(e1) / 8, st)
         lat.close()
     fa = res["exact"][0]
-    for name in ("fp32", "tensor"):
+    for name in ("fp32", "tensor", "mma"):
         fb, ms, st = res[name]
         assert np.abs(fa["n"] - fb["n"]).max() < 1e-5
         assert np.abs(fa["ux"] - fb["ux"]).max() < 1e-5
