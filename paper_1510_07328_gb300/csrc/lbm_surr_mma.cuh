@@ -88,33 +88,44 @@ __device__ __forceinline__ void net_mtile(const unsigned char* sW, int lane, uin
     h[4 * p + 2] = tc::silu2_packed(d1[0]);
     h[4 * p + 3] = tc::silu2_packed(d1[1]);
   }
-  // h[4c .. 4c + 3] is the A fragment of K chunk c of layer 2.  The SiLU of
-  // layer-2 n-tiles 2p, 2p + 1 is the A fragment of K chunk p of layer 3,
-  // which is consumed at once.
+  // h[4c .. 4c + 3] is the A fragment of K chunk c of layer 2.  Its eight
+  // n-tiles accumulate side by side (eight independent MMA chains); their
+  // SiLU, in place, gives the four A fragments of layer 3.
+  uint32_t d[16];  // layer-2 accumulators: d[2 nt] row g, d[2 nt + 1] row g + 8
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const uint2 c = lds2(sW + kMmC2 + (p * 4 + t) * 8);  // b2/2 of n-tiles 2p, 2p + 1 (FP16 pairs)
+    d[4 * p + 0] = c.x;
+    d[4 * p + 1] = c.x;
+    d[4 * p + 2] = c.y;
+    d[4 * p + 3] = c.y;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const uint4 b = lds4(sW + kMmB2 + ((k * 4 + p) * 32 + lane) * 16);
+      mma_k16_h(*reinterpret_cast<uint32_t(*)[2]>(d + 4 * p), h + 4 * k, b.x, b.y);
+      mma_k16_h(*reinterpret_cast<uint32_t(*)[2]>(d + 4 * p + 2), h + 4 * k, b.z, b.w);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) d[i] = tc::silu2_packed(d[i]);
+  // layer 3: the hi and lo weights as two chains, summed at the end
   const float2 b3 = ldsf2(sW + kMmC3);
+  float yl[4] = {0.f, 0.f, 0.f, 0.f};
   y[0] = t == 0 ? b3.x : 0.0f;
   y[1] = t == 0 ? b3.y : 0.0f;
   y[2] = y[0];
   y[3] = y[1];
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    const uint2 c = lds2(sW + kMmC2 + (p * 4 + t) * 8);  // b2/2 of n-tiles 2p, 2p + 1 (FP16 pairs)
-    uint32_t d0[2] = {c.x, c.x}, d1[2] = {c.y, c.y};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const uint4 b = lds4(sW + kMmB2 + ((k * 4 + p) * 32 + lane) * 16);
-      mma_k16_h(d0, h + 4 * k, b.x, b.y);
-      mma_k16_h(d1, h + 4 * k, b.z, b.w);
-    }
-    uint32_t a3[4];
-    a3[0] = tc::silu2_packed(d0[0]);
-    a3[1] = tc::silu2_packed(d0[1]);
-    a3[2] = tc::silu2_packed(d1[0]);
-    a3[3] = tc::silu2_packed(d1[1]);
-    const uint4 b = lds4(sW + kMmB3 + (p * 32 + lane) * 16);
-    mma_k16(y, a3, b.x, b.y);  // W3 hi
-    mma_k16(y, a3, b.z, b.w);  // W3 lo
+  for (int k = 0; k < 4; ++k) {
+    const uint4 b = lds4(sW + kMmB3 + (k * 32 + lane) * 16);
+    mma_k16(y, d + 4 * k, b.x, b.y);   // W3 hi
+    mma_k16(yl, d + 4 * k, b.z, b.w);  // W3 lo
   }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) y[i] += yl[i];
 }
 
 // Network outputs (y_0, y_1) of this lane's cell; every lane of the warp
