@@ -173,8 +173,16 @@ __global__ void __launch_bounds__(kTileX, sizeof(T) == 8 ? 4 : 6) stream_collide
     const int x0 = (lt - ty * P.tiles_x) * kTileX;
     const int x = x0 + (int)threadIdx.x;
     const int y0 = ty * TY, y1 = min(y0 + TY, P.ny);
-    const bool clean = tile_clean(P, x0, y0, y1);
     const bool xin = x0 >= 1 && x0 + kTileX <= P.nx - 1;
+    // deviations: the first row's obstacle-free pull is issued before the
+    // mask scan, so that both latencies overlap; a tile with solid cells in
+    // reach pulls that row again with the checks (the first pull reads only
+    // cells of the lattice, solid ones included, and is discarded)
+    float gn[9];
+    if constexpr (Stor<T>::dev) {
+      if (x < P.nx) gather_dev(fin, plane, P, x, y0, xin, gn);
+    }
+    const bool clean = tile_clean(P, x0, y0, y1);
     if (x < P.nx) {
       if constexpr (Stor<T>::dev) {
         // pulled deviations of row y into g; false for a solid cell
@@ -191,8 +199,8 @@ __global__ void __launch_bounds__(kTileX, sizeof(T) == 8 ? 4 : 6) stream_collide
           return true;
         };
         // the next row's loads are issued before the current row's collision
-        float gn[9];
-        bool fn = load(y0, gn);
+        bool fn = true;
+        if (!clean) fn = load(y0, gn);
 #pragma unroll 1
         for (int y = y0; y < y1; ++y) {
           float g[9];
