@@ -1,7 +1,8 @@
 // Minimal tcgen05 (5th-generation tensor core) helpers for sm_100-family
 // GPUs: TMEM allocation, shared-memory matrix descriptors for the canonical
-// K-major layout without swizzle, the f16-kind MMA with an FP32 accumulator
-// in TMEM, commit to an mbarrier, bounded waits and TMEM loads.
+// K-major layout without swizzle, the f16-kind MMA with an FP32 or FP16
+// accumulator in TMEM, commit to an mbarrier, bounded waits, TMEM loads, and
+// the packed FP16 SiLU both tensor-core engines use.
 //
 // Canonical K-major layout (no swizzle): an R x K operand of 16-bit elements
 // is cut into core matrices of 8 rows x 8 elements (8 rows of 16 bytes, 128
@@ -92,46 +93,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int li
   return done != 0;
 }
 
-// 64 consecutive FP32 columns of this thread's TMEM lane (32x32b shape: warp w
-// of the CTA reads lanes 32 w .. 32 w + 31).
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
-  uint32_t r[64];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%"
-      "28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%"
-      "54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
-        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
-        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
-        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
-        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int c = 0; c < 64; ++c) v[c] = __uint_as_float(r[c]);
-}
-
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%"
-      "28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
-}
-
 // 64 consecutive 16-bit columns of this thread's TMEM lane (an FP16
 // accumulator), packed in pairs: r[i] holds columns 2i (low half) and 2i + 1
 // (the .x32 repetition count counts the 32-bit registers written).
@@ -159,33 +120,12 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
   for (int c = 0; c < 4; ++c) v[c] = __uint_as_float(r[c]);
 }
 
-// SiLU of two values in FP16: silu(z) = (z/2)(1 + tanh(z/2)), one packed
-// tanh.approx.f16x2 for both (about 1e-3 relative, the order of the FP16
-// rounding the tensor-core operands carry anyway).
-__device__ __forceinline__ __half2 silu2_h(float z0, float z1) {
-  const __half2 hz = __floats2half2_rn(0.5f * z0, 0.5f * z1);
-  uint32_t t;
-  asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(*reinterpret_cast<const uint32_t*>(&hz)));
-  const __half2 th = *reinterpret_cast<const __half2*>(&t);
-  return __hfma2(hz, th, hz);
-}
-
 // SiLU of a packed FP16 pair of halved arguments h = z/2: h + h tanh(h).
 __device__ __forceinline__ uint32_t silu2_packed(uint32_t h) {
   uint32_t t;
   asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(h));
   const __half2 hv = *reinterpret_cast<const __half2*>(&h), tv = *reinterpret_cast<const __half2*>(&t);
   const __half2 s = __hfma2(hv, tv, hv);
-  return *reinterpret_cast<const uint32_t*>(&s);
-}
-
-// The same from the halved arguments h = z/2 (weights pre-scaled by 1/2):
-// silu(z) = h + h tanh(h); returns the packed FP16 pair.
-__device__ __forceinline__ uint32_t silu2_half_arg(float h0, float h1) {
-  const __half2 hz = __floats2half2_rn(h0, h1);
-  uint32_t t;
-  asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(*reinterpret_cast<const uint32_t*>(&hz)));
-  const __half2 s = __hfma2(hz, *reinterpret_cast<const __half2*>(&t), hz);
   return *reinterpret_cast<const uint32_t*>(&s);
 }
 
