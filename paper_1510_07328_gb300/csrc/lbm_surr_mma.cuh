@@ -1,11 +1,12 @@
 // The FD step with the learned inversion, the network evaluated by each warp
 // on its own 32 cells with warp-level MMAs (mma.sync, FP16 operands,
-// accumulators in registers: FP16 for the hidden layers, FP32 for the output).  Same network, input split, polish, residual
-// check and fallback as the tcgen05 engine (lbm_surr.cuh); what differs is
-// where the activations live.  The accumulator fragment of an m16n8 MMA holds
-// the same (row, column) pairs as the A fragment of the next K = 16 MMA, so a
-// layer's SiLU output feeds the next layer straight from registers: no shared
-// memory round trip, no tensor memory, no barrier between the warps of a CTA.
+// accumulators in registers: FP16 for the hidden layers, FP32 for the
+// output).  Same network, input split, polish, residual check and fallback as
+// the tcgen05 engine (lbm_surr.cuh); what differs is where the activations
+// live.  The accumulator fragment of an m16n8 MMA holds the same (row,
+// column) pairs as the A fragment of the next K = 16 MMA, so a layer's SiLU
+// output feeds the next layer straight from registers: no shared memory round
+// trip, no tensor memory, no barrier between the warps of a CTA.
 #pragma once
 #include "lbm_surr.cuh"
 
