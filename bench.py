@@ -255,13 +255,14 @@ def kernel_source_hash(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str, cells: int):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the kernel source as it is now (else None)."""
+def profiled_traffic(kernel: str, workload: str, cells: int):
+    """DRAM bytes per launch from the committed ncu summary of this kernel on
+    this workload, if it was taken on the kernel source as it is now (else
+    None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))
-        e = d[kernel]
+        e = d[f"{kernel}@{workload}"]
         if e["source_hash"] != kernel_source_hash(kernel):
             return None
         return e["dram_bytes_per_cell"] * cells
@@ -507,7 +508,7 @@ def run_ours(a, world, rank, local):
     if a.workload == "d1v3":
         kname = "stream_collide_d1<%s,%s>" % ({"f32": "float", "bf16": "bf16", "f64": "double"}[a.prec],
                                               a.stat.upper())
-    traffic = profiled_traffic(kname, cells)
+    traffic = profiled_traffic(kname, a.workload, cells)
     out = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
