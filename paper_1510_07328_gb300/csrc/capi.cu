@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "io_dev.cuh"
 #include "launch.h"
 #include "lbm.h"
 #include "lbm_kernels.cuh"
@@ -223,17 +224,32 @@ void launch_init_t(lbm_ctx* c, const ProbDev& P, const InitDesc& d) {
   const int64_t cells = (int64_t)P.nx * P.ny;
   T* f = (T*)c->buf[c->cur];
   const unsigned g = blocks_for(cells, 256);
-  switch (c->stat) {
-    case LBM_STAT_FD: init_kernel<T, STAT_FD><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
-    case LBM_STAT_FD_T0: init_kernel<T, STAT_T0><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
-    default: init_kernel<T, STAT_MB><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
+  // deviation storage: the FP32 equilibrium of the reduced-precision step
+  if constexpr (Stor<T>::dev) {
+    switch (c->stat) {
+      case LBM_STAT_FD: init_dev_kernel<T, STAT_FD><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
+      case LBM_STAT_FD_T0: init_dev_kernel<T, STAT_T0><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
+      default: init_dev_kernel<T, STAT_MB><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
+    }
+  } else {
+    switch (c->stat) {
+      case LBM_STAT_FD: init_kernel<T, STAT_FD><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
+      case LBM_STAT_FD_T0: init_kernel<T, STAT_T0><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
+      default: init_kernel<T, STAT_MB><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
+    }
   }
 }
 
 template <class T, int STAT>
 void launch_moments_t(lbm_ctx* c, const ProbDev& P, double* o[6], unsigned g) {
-  moments_kernel<T, STAT><<<g, kMomThreads, 0, c->stream>>>((const T*)c->buf[c->cur], P, c->plane, c->lim, c->limf, o[0], o[1],
-                                                             o[2], o[3], o[4], o[5], c->partials);
+  // deviation storage: the closure quantities from the FP32 inversion
+  if constexpr (Stor<T>::dev)
+    moments_dev_kernel<T, STAT><<<g, kMomThreads, 0, c->stream>>>((const T*)c->buf[c->cur], P, c->plane, c->lim,
+                                                                  c->limf, o[0], o[1], o[2], o[3], o[4], o[5],
+                                                                  c->partials);
+  else
+    moments_kernel<T, STAT><<<g, kMomThreads, 0, c->stream>>>((const T*)c->buf[c->cur], P, c->plane, c->lim, c->limf,
+                                                               o[0], o[1], o[2], o[3], o[4], o[5], c->partials);
 }
 
 template <class T>
