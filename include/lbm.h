@@ -64,7 +64,10 @@ typedef enum { LBM_STAT_FD = 0, LBM_STAT_FD_T0 = 1, LBM_STAT_MB = 2 } lbm_stat;
 /* Population storage.  F64: f itself in FP64, all arithmetic FP64.
  * F32_DEV / BF16_DEV: the deviation g_a = f_a - W_a^ref from a per-problem
  * constant W^ref = w_a(J_2(t_ref)) n_ref, stored in FP32 / BF16, moment sums
- * and equilibrium in FP32. */
+ * and equilibrium in FP32.  These contexts also initialise in FP32 (the
+ * step's deviation-form equilibrium, closure from t in FP32), and
+ * lbm_moments takes x, t, T and mu from the FP32 inversion (n, u and the
+ * diag sums stay FP64 sums of the stored values). */
 typedef enum { LBM_F64 = 0, LBM_F32_DEV = 1, LBM_BF16_DEV = 2 } lbm_prec;
 
 typedef enum { LBM_INV_EXACT = 0, LBM_INV_SURROGATE = 1 } lbm_inv;
