@@ -56,6 +56,31 @@ def test_create_rejects_bad_problem(lib, bad, msg):
     assert msg in str(e.value)
 
 
+@pytest.mark.parametrize("shape,msg", [
+    ((1 << 21, 1 << 20), "problem too large"),      # 2^41 cells in one problem
+    ((65536, 32769), "more than 2^31 cells"),       # 2^31 + 65536 cells: 32-bit plane offsets
+])
+def test_create_rejects_oversize(lib, shape, msg):
+    """Maximum sizes: one problem above 2^40 cells, or a context whose planes
+    exceed the 32-bit offsets of the step kernels, is refused before any
+    allocation."""
+    p = dict(nx=shape[0], ny=shape[1], tau=0.8, bc_x="periodic", bc_y="periodic", n_ref=1.0, t_ref=0.05)
+    for prec in ("f32", "f64"):
+        with pytest.raises(lib.LbmError) as e:
+            lib.lbm_create([p], prec=prec)
+        assert e.value.status == lib.LBM_EINVAL
+        assert msg in str(e.value)
+
+
+def test_create_rejects_too_many_cells_over_problems(lib):
+    """The 2^31-cell limit counts the padded planes of all problems together."""
+    p = dict(nx=32768, ny=32768, tau=0.8, bc_x="periodic", bc_y="periodic", n_ref=1.0, t_ref=0.05)
+    with pytest.raises(lib.LbmError) as e:
+        lib.lbm_create([p, p, dict(p, nx=8, ny=8)], prec="f32")
+    assert e.value.status == lib.LBM_EINVAL
+    assert "more than 2^31 cells" in str(e.value)
+
+
 def test_create_rejects_reference_out_of_range(lib):
     p = dict(nx=8, ny=4, tau=0.8, n_ref=1.0, t_ref=20.0)
     with pytest.raises(lib.LbmError) as e:
