@@ -53,7 +53,7 @@ def parse():
                          "d1v3: the zero-temperature Riemann run of the paper's Fig. 1 on d1v3, scaled to --cells1d; "
                          "porous: the paper's porous sample (porosity 0.992, discs of radius 3) scaled to L x L")
     ap.add_argument("--cells1d", type=int, default=1 << 25, help="lattice length of the d1v3 workload")
-    ap.add_argument("--autotune", action="store_true", help="autotune the tiling before timing (always on for batched)")
+    ap.add_argument("--autotune", action="store_true", help="autotune the tiling before timing (always on for batched and porous)")
     ap.add_argument("--inv", default="exact", choices=["exact", "surrogate"],
                     help="per-cell FD inversion: exact, or the learned network (trained first, on 1e6 pairs)")
     ap.add_argument("--train-epochs", type=int, default=32)
@@ -442,7 +442,7 @@ def run_ours(a, world, rank, local):
         lat.step(a.warmup)
     torch.cuda.synchronize()
     tiling = None
-    if a.workload == "batched" or a.autotune:
+    if a.workload in ("batched", "porous") or a.autotune:
         with torch.cuda.stream(stream):
             tiling = lbm.lbm_autotune(lat.ctx, 3)
     cfg = workload_config(a, world, probs, tiling)
