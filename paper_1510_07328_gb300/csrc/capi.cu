@@ -243,13 +243,8 @@ void launch_init_t(lbm_ctx* c, const ProbDev& P, const InitDesc& d) {
 template <class T, int STAT>
 void launch_moments_t(lbm_ctx* c, const ProbDev& P, double* o[6], unsigned g) {
   // deviation storage: the closure quantities from the FP32 inversion
-  if constexpr (Stor<T>::dev)
-    moments_dev_kernel<T, STAT><<<g, kMomThreads, 0, c->stream>>>((const T*)c->buf[c->cur], P, c->plane, c->lim,
-                                                                  c->limf, o[0], o[1], o[2], o[3], o[4], o[5],
-                                                                  c->partials);
-  else
-    moments_kernel<T, STAT><<<g, kMomThreads, 0, c->stream>>>((const T*)c->buf[c->cur], P, c->plane, c->lim, c->limf,
-                                                               o[0], o[1], o[2], o[3], o[4], o[5], c->partials);
+  moments_kernel<T, STAT, Stor<T>::dev><<<g, kMomThreads, 0, c->stream>>>(
+      (const T*)c->buf[c->cur], P, c->plane, c->lim, c->limf, o[0], o[1], o[2], o[3], o[4], o[5], c->partials);
 }
 
 template <class T>

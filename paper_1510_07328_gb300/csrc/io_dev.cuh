@@ -1,11 +1,8 @@
-// Initial state and moments of deviation-stored contexts (FP32 or BF16
-// g = f - W_ref), computed with the reduced-precision step's own arithmetic:
-// the equilibrium in FP32 deviation form, the Fermi-Dirac closure and the
-// inversion in FP32.  Sums, density and velocity in the moments stay FP64
-// (additions of the stored values), so the conservation diagnostics keep
-// their precision; only the closure quantities (x, t, T, mu, and at
-// initialisation J_2, J_4 from t) are FP32, with errors of the order of one
-// FP32 step.
+// Initial state of deviation-stored contexts (FP32 or BF16 g = f - W_ref),
+// computed with the reduced-precision step's own arithmetic: the equilibrium
+// in FP32 deviation form and the Fermi-Dirac closure from t in FP32, with
+// errors of the order of one FP32 step.  (Their moments take the closure
+// quantities from the FP32 inversion: moments_kernel with F32CL.)
 #pragma once
 #include "lbm_dev32.cuh"
 
@@ -88,87 +85,6 @@ __global__ void init_dev_kernel(T* __restrict__ f, ProbDev P, int64_t plane, Ini
   const float g0[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const int c = (int)(P.base + (int64_t)y * P.pitch + x);
   relax_store_dev<T, STAT>(Q, g0, m, 1.5f - delta, J4, f, plane, c);
-}
-
-// Moments of a deviation-stored context: as moments_kernel (FP64 sums of
-// W_ref + g, density, velocity, the diagnostics), with the FD inversion,
-// t = 1/f_1(x), theta and mu from the FP32 inversion of the step.
-template <class T, int STAT>
-__global__ void __launch_bounds__(kMomThreads) moments_dev_kernel(const T* __restrict__ f, ProbDev P, int64_t plane,
-                                                                  InvLimits L, InvLimitsF Lf, double* __restrict__ on,
-                                                                  double* __restrict__ oux, double* __restrict__ ouy,
-                                                                  double* __restrict__ oT, double* __restrict__ omu,
-                                                                  double* __restrict__ ot, double* __restrict__ partials) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t cells = (int64_t)P.nx * P.ny;
-  double acc[kNPartial] = {0, 0, 0, 0, 0, 0};
-  const int64_t c = i < cells ? P.base + (int64_t)(i / P.nx) * P.pitch + (int)(i % P.nx) : 0;
-  if (i < cells && P.solid != nullptr && P.solid[c] != 0) {  // obstacle: no fluid
-    if (on) on[i] = 0.0;
-    if (oux) oux[i] = 0.0;
-    if (ouy) ouy[i] = 0.0;
-    if (oT) oT[i] = 0.0;
-    if (omu) omu[i] = 0.0;
-    if (ot) ot[i] = 0.0;
-  } else if (i < cells) {
-    double v[9];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) v[a] = Stor<T>::to_f64(f[a * plane + c], P.wref[a]);
-    const double n = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
-    const double jx = (v[1] - v[3]) + (v[5] - v[6]) + (v[8] - v[7]);
-    const double jy = (v[2] - v[4]) + (v[5] + v[6]) - (v[7] + v[8]);
-    const double E = ((v[1] + v[2]) + (v[3] + v[4])) + 2.0 * ((v[5] + v[6]) + (v[7] + v[8]));
-    const double ux = jx / n, uy = jy / n;
-    double theta = 0.0, mu = 0.0, t = 0.0;
-    int cl = 0;
-    if (STAT == STAT_FD) {
-      const double J2 = 1.5 * (E / n - (ux * ux + uy * uy));
-      cl = (J2 >= L.j2_hi || J2 <= L.j2_lo) ? 1 : 0;
-      float xf;
-      j4_from_delta_f((float)(1.5 - J2), Lf, &xf);
-      const float tf = 1.0f / (fmaxf(xf, 0.0f) + log1pf(expf(-fabsf(xf))));  // t = T/T_F = 1/f_1(x)
-      t = (double)tf;
-      theta = n * t / (2.0 * kPi);  // theta = n t/(2 pi), T_F = n/(2 pi)
-      mu = theta * (double)xf;
-    } else if (STAT == STAT_T0) {
-      theta = 0.0; t = 0.0; mu = n / (2.0 * kPi);
-    } else {
-      theta = mu = t = __longlong_as_double(0x7ff8000000000000LL);
-    }
-    if (on) on[i] = n;
-    if (oux) oux[i] = (jx + 0.5 * P.fx) / n;  // velocity at the time level under a body force
-    if (ouy) ouy[i] = (jy + 0.5 * P.fy) / n;
-    if (oT) oT[i] = theta;
-    if (omu) omu[i] = mu;
-    if (ot) ot[i] = t;
-    acc[0] = n; acc[1] = jx; acc[2] = jy; acc[3] = E;
-    acc[4] = cl;
-    bool fin = isfinite(n) && isfinite(jx) && isfinite(jy) && isfinite(E);
-#pragma unroll
-    for (int a = 0; a < 9; ++a) fin = fin && isfinite(v[a]);
-    acc[5] = fin ? 0.0 : 1.0;
-  }
-  // fixed-order block reduction: warp shuffle tree, then warps in order
-  __shared__ double sh[kMomThreads / 32][kNPartial];
-#pragma unroll
-  for (int k = 0; k < kNPartial; ++k) {
-    double s = acc[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    acc[k] = s;
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < kNPartial; ++k) sh[wid][k] = acc[k];
-  }
-  __syncthreads();
-  if (threadIdx.x < kNPartial) {
-    double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < kMomThreads / 32; ++w) s += sh[w][threadIdx.x];
-    partials[(int64_t)blockIdx.x * kNPartial + threadIdx.x] = s;
-  }
 }
 
 }  // namespace lbm
