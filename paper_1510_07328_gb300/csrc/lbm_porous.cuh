@@ -99,28 +99,25 @@ __device__ __forceinline__ void relax_force_store_dev(const ProbDev& P, const fl
   // force: d = F/n, rr = 2 u.d + |d|^2
   const float dx = P.f.fx * m.in, dy = P.f.fy * m.in;
   const float rr = fmaf(2.0f, fmaf(ux, dx, uy * dy), fmaf(dx, dx, dy * dy));
-  float ge[9], gf[9];
-  ge[0] = fmaf(W0, q0 * u2, dW0);
-  gf[0] = W0 * (q0 * rr);
+  // each population is stored as soon as its equilibrium and force parts
+  // are formed (no arrays of nine live across the cell)
+  auto put = [&](int a, float ge, float gf) { fout[a * plane + off] = Dev<T>::st(fmaf(w, ge - g[a], g[a]) + gf); };
+  put(0, fmaf(W0, q0 * u2, dW0), W0 * (q0 * rr));
   auto pair = [&](float eu, float ed, float A, float qc, float c1, float W, float dW, int ap, int am) {
     const float e2 = eu * eu;
     const float base = fmaf(W, fmaf(a2, e2, qc * u2), dW);
     const float wo = W * (eu * fmaf(bk, e2, A));
-    ge[ap] = base + wo;
-    ge[am] = base - wo;
     const float pp = eu + ed;
     const float bc1 = b0 * c1;
     const float even = fmaf(qc, rr, a2 * ed * fmaf(2.0f, eu, ed));
     const float odd = fmaf(ed, fmaf(bc1, rr, A), fmaf(bc1 * eu, rr, bk * ed * fmaf(pp, pp + eu, e2)));
-    gf[ap] = W * (even + odd);
-    gf[am] = W * (even - odd);
+    put(ap, base + wo, W * (even + odd));
+    put(am, base - wo, W * (even - odd));
   };
   pair(ux, dx, A1, q1, c1s, Ws, dWs, 1, 3);
   pair(uy, dy, A1, q1, c1s, Ws, dWs, 2, 4);
   pair(ux + uy, dx + dy, A2, q2, c1l, Wl, dWl, 5, 7);
   pair(ux - uy, dx - dy, A2, q2, c1l, Wl, dWl, 8, 6);
-#pragma unroll
-  for (int a = 0; a < 9; ++a) fout[a * plane + off] = Dev<T>::st(fmaf(w, ge[a] - g[a], g[a]) + gf[a]);
 }
 
 // True when the tile (kTileX cells from x0, rows y0 .. y1 - 1) and its halo of
@@ -159,7 +156,7 @@ __device__ __forceinline__ bool tile_clean(const ProbDev& P, int x0, int y0, int
 // solid cells in reach take the pull without mask checks (for FP32 / BF16 the
 // branch-free interior gather).
 template <class T, int STAT, int TY, bool PERSIST>
-__global__ void __launch_bounds__(kTileX, sizeof(T) == 8 ? 4 : 6) stream_collide_porous(const T* __restrict__ fin, T* __restrict__ fout,
+__global__ void __launch_bounds__(kTileX, sizeof(T) == 8 ? 4 : (STAT == STAT_FD ? 6 : 8)) stream_collide_porous(const T* __restrict__ fin, T* __restrict__ fout,
                                                                 const ProbDev* __restrict__ probs, int nprob,
                                                                 int ntiles, int64_t plane, InvLimits L,
                                                                 InvLimitsF Lf) {
