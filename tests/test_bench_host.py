@@ -1,0 +1,39 @@
+"""bench.py's host-side pieces, without a GPU: the closure each workload runs
+with, and the CPU oracle's bounded sample of every workload (the reference
+arm), one step at reduced sizes."""
+import argparse
+import os
+import sys
+
+import numpy as np
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def args(workload, stat="fd"):
+    return argparse.Namespace(workload=workload, stat=stat, L=512, cells1d=1 << 14, tau=0.8, steps=1, warmup=0,
+                              prec="f32", inv="exact", engine="tensor")
+
+
+@pytest.mark.parametrize("workload,stat,want", [
+    ("smooth_t", "fd", "fd"), ("batched", "fd", "fd"), ("d1v3", "fd", "t0"), ("porous", "fd", "mb"),
+    ("d1v3", "mb", "mb"), ("porous", "t0", "t0"),
+])
+def test_settle_closure(workload, stat, want):
+    a = args(workload, stat)
+    bench.settle_closure(a)
+    assert a.stat == want
+
+
+@pytest.mark.parametrize("workload", ["smooth_t", "batched", "d1v3", "porous"])
+def test_oracle_sample_takes_a_finite_step(workload):
+    a = args(workload)
+    bench.settle_closure(a)
+    step, f, cells, what = bench.oracle_workload(a)
+    assert cells == f[0].size and cells > 0 and what
+    g = step(f)
+    assert g.shape == f.shape and np.isfinite(g).all()
+    # one collision conserves the mass of the sample (periodic wrap)
+    assert abs(g.sum() - f.sum()) < 1e-12 * abs(f.sum())
