@@ -166,6 +166,20 @@ __device__ __forceinline__ FD5f fd_eval_deg_f(float x) {
   return r;
 }
 
+// Starting value of the general branch (J_2(x_lo) < J_2 <= 1.35): x as a
+// degree-6 polynomial in v = ln((J_2 - 1)/(3/2 - J_2)), largest error 8.2e-5
+// over x in [x(t = 10) - 0.05, x(J_2 = 1.35) + 0.3] (least-squares fit to
+// J_2 = f_2^2/(f_1 f_3) from mpmath's polylogarithm; fit_x_of_j2.py).
+__device__ __forceinline__ float x_start_general(float J2) {
+  constexpr float c[7] = {-4.432891559e-05f, -8.445504196e-05f, 6.418418863e-03f, 7.015894638e-02f,
+                          3.457496236e-01f,  1.903373951e+00f,  2.431948916e+00f};
+  const float v = __logf(__fdividef(J2 - 1.0f, 1.5f - J2));
+  float x = c[0];
+#pragma unroll
+  for (int k = 1; k < 7; ++k) x = fmaf(x, v, c[k]);
+  return x;
+}
+
 // J_4 from delta = 3/2 - J_2 in FP32 (the exact inversion, to FP32
 // resolution; *xout receives x).
 //  * non-finite input: propagated at once;
@@ -177,8 +191,8 @@ __device__ __forceinline__ FD5f fd_eval_deg_f(float x) {
 //    returning x + dx and J_4 + J_4' dx (second-order remainder < 1e-7).
 //    J_2' = J_2 (2 f_1/f_2 - f_0/f_1 - f_2/f_3), J_4' = J_4 (2 f_2/f_3 -
 //    f_1/f_2 - f_3/f_4), from d f_n/dx = f_{n-1};
-//  * otherwise (J_2 < 4/3): safeguarded Newton with the general FP32
-//    evaluation, at most 24 evaluations.
+//  * otherwise (J_2 <= 1.35): safeguarded Newton with the general FP32
+//    evaluation from the fitted start x_start_general, at most 24 evaluations.
 __device__ __forceinline__ float j4_from_delta_f(float delta, const InvLimitsF& L, float* xout) {
   const float J2 = 1.5f - delta;
   if (!(J2 == J2)) {  // non-finite state: propagate without iterating
@@ -226,7 +240,10 @@ __device__ __forceinline__ float j4_from_delta_f(float delta, const InvLimitsF& 
       x += dx;
     }
   }
-  float x = 1.0f, lo = L.x_lo, hi = 6.0f;  // J_2(6) = 1.40 > 4/3: the root lies below
+  // J_2 <= 1.35: the root lies below x = 4.34 (J_2(6) = 1.40).  Newton starts
+  // from the fitted x(J_2) (within 1e-4), so one evaluation usually ends it.
+  float lo = L.x_lo, hi = 6.0f;
+  float x = fminf(fmaxf(x_start_general(J2), lo), hi);
   float J4 = 0.0f;
 #pragma unroll 1
   for (int it = 0; it < 24; ++it) {
