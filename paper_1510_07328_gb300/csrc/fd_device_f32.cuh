@@ -166,17 +166,20 @@ __device__ __forceinline__ FD5f fd_eval_deg_f(float x) {
   return r;
 }
 
-// Starting value of the general branch (J_2(x_lo) < J_2 <= 1.35): x as a
-// degree-6 polynomial in v = ln((J_2 - 1)/(3/2 - J_2)), largest error 8.2e-5
-// over x in [x(t = 10) - 0.05, x(J_2 = 1.35) + 0.3] (least-squares fit to
-// J_2 = f_2^2/(f_1 f_3) from mpmath's polylogarithm; fit_x_of_j2.py).
+// 3/2 - J_2 at x = 7: below it the degenerate root with tail passes is exact.
+constexpr float kDelta7 = 0.078501010f;
+
+// Starting value of the Newton branch (J_2(x_lo) < J_2 <= J_2(7)): x as a
+// degree-8 polynomial in v = ln((J_2 - 1)/(3/2 - J_2)), largest error 4.0e-5
+// over x in [x(t = 10) - 0.05, 7.3] (least-squares fit to J_2 = f_2^2/(f_1 f_3)
+// from mpmath's polylogarithm; fit_x_of_j2.py).
 __device__ __forceinline__ float x_start_general(float J2) {
-  constexpr float c[7] = {-4.432891559e-05f, -8.445504196e-05f, 6.418418863e-03f, 7.015894638e-02f,
-                          3.457496236e-01f,  1.903373951e+00f,  2.431948916e+00f};
+  constexpr float c[9] = {5.482719542e-06f, 6.089144600e-05f, 1.952511272e-04f, 2.676517802e-04f, 6.391339607e-03f,
+                          6.971210059e-02f, 3.455914096e-01f, 1.903484720e+00f, 2.431969767e+00f};
   const float v = __logf(__fdividef(J2 - 1.0f, 1.5f - J2));
   float x = c[0];
 #pragma unroll
-  for (int k = 1; k < 7; ++k) x = fmaf(x, v, c[k]);
+  for (int k = 1; k < 9; ++k) x = fmaf(x, v, c[k]);
   return x;
 }
 
@@ -184,15 +187,16 @@ __device__ __forceinline__ float x_start_general(float J2) {
 // resolution; *xout receives x).
 //  * non-finite input: propagated at once;
 //  * J_2 beyond the clamp interval: x at the nearest end;
-//  * degenerate regime (delta < 0.15, x > 4.2): the quadratic root; closed
-//    form J_4 for x >= 17; one tail pass for x >= 9, two for x >= 7; below
-//    that Newton steps on J_2(x) from the second pass, each with one
-//    evaluation of f_0..f_4, stopping when the step is below 5e-4 x and
-//    returning x + dx and J_4 + J_4' dx (second-order remainder < 1e-7).
+//  * degenerate regime (delta < 3/2 - J_2(7), x > 7): the quadratic root;
+//    closed form J_4 for x >= 17; otherwise one tail pass for x >= 9, two
+//    below;
+//  * otherwise safeguarded Newton on J_2(x) from the fitted start
+//    x_start_general (within 4e-5), each step one evaluation of f_0..f_4
+//    (three-term series for x >= 4), stopping when the step is below
+//    5e-4 |x| and returning x + dx and J_4 + J_4' dx (second-order
+//    remainder < 1e-7): one evaluation in practice, at most 24.
 //    J_2' = J_2 (2 f_1/f_2 - f_0/f_1 - f_2/f_3), J_4' = J_4 (2 f_2/f_3 -
-//    f_1/f_2 - f_3/f_4), from d f_n/dx = f_{n-1};
-//  * otherwise (J_2 <= 1.35): safeguarded Newton with the general FP32
-//    evaluation from the fitted start x_start_general, at most 24 evaluations.
+//    f_1/f_2 - f_3/f_4), from d f_n/dx = f_{n-1}.
 __device__ __forceinline__ float j4_from_delta_f(float delta, const InvLimitsF& L, float* xout) {
   const float J2 = 1.5f - delta;
   if (!(J2 == J2)) {  // non-finite state: propagate without iterating
@@ -208,46 +212,23 @@ __device__ __forceinline__ float j4_from_delta_f(float delta, const InvLimitsF& 
     *xout = L.x_lo;
     return f.f3 * f.f3 * rcp_a(f.f2 * f.f4);
   }
-  if (delta < 0.15f) {
+  if (delta < kDelta7) {
     const float s = deg_root_f(delta);
     if (s >= kXDegF * kXDegF) {
       *xout = sqrt_a(s);
       return j4_degenerate_f(s);
     }
     float x = tail_pass_f(delta, sqrt_a(s));
-    if (x >= 9.0f) {
-      *xout = x;
-      return j4_tail_f(x);
-    }
-    x = tail_pass_f(delta, x);
-    if (x >= 7.0f) {
-      *xout = x;
-      return j4_tail_f(x);
-    }
-#pragma unroll 1
-    for (int it = 0; it < 4; ++it) {
-      const FD5f f = fd_eval_deg_f(x);
-      const float i1 = rcp_a(f.f1), i2 = rcp_a(f.f2), i3 = rcp_a(f.f3), i4 = rcp_a(f.f4);
-      const float j = f.f2 * f.f2 * i1 * i3;
-      const float dj = j * (2.0f * f.f1 * i2 - f.f0 * i1 - f.f2 * i3);
-      const float dx = (J2 - j) * rcp_a(dj);
-      const float J4 = f.f3 * f.f3 * i2 * i4;
-      if (fabsf(dx) < 5e-4f * x || it == 3) {
-        const float dJ4 = J4 * (2.0f * f.f2 * i3 - f.f1 * i2 - f.f3 * i4);
-        *xout = x + dx;
-        return J4 + dJ4 * dx;
-      }
-      x += dx;
-    }
+    if (x < 9.0f) x = tail_pass_f(delta, x);
+    *xout = x;
+    return j4_tail_f(x);
   }
-  // J_2 <= 1.35: the root lies below x = 4.34 (J_2(6) = 1.40).  Newton starts
-  // from the fitted x(J_2) (within 1e-4), so one evaluation usually ends it.
-  float lo = L.x_lo, hi = 6.0f;
+  float lo = L.x_lo, hi = 8.0f;  // J_2(8) > J_2(7): the root lies below
   float x = fminf(fmaxf(x_start_general(J2), lo), hi);
   float J4 = 0.0f;
 #pragma unroll 1
   for (int it = 0; it < 24; ++it) {
-    const FD5f f = fd_eval_f(x);
+    const FD5f f = x >= 4.0f ? fd_eval_deg_f(x) : fd_eval_f(x);
     const float i1 = rcp_a(f.f1), i2 = rcp_a(f.f2), i3 = rcp_a(f.f3), i4 = rcp_a(f.f4);
     const float j = f.f2 * f.f2 * i1 * i3;
     const float g = j - J2;

@@ -1,9 +1,10 @@
-"""Generator of the starting value of the FP32 inversion's general branch
-(csrc/fd_device_f32.cuh, kXStart): a degree-6 least-squares fit of x as a
-polynomial in v = ln((J_2 - 1)/(3/2 - J_2)) over the branch's interval.
+"""Generator of the starting value of the FP32 inversion's Newton branch
+(csrc/fd_device_f32.cuh, x_start_general): a degree-8 least-squares fit of x
+as a polynomial in v = ln((J_2 - 1)/(3/2 - J_2)) over the branch's interval.
 
-The branch serves J_2 in (J_2(x_lo), 1.35], x_lo = x(t = 10).  The fit runs
-over x in [x_lo - 0.05, x(J_2 = 1.35) + 0.3].  v follows both ends:
+The branch serves J_2 in (J_2(x_lo), J_2(7)], x_lo = x(t = 10); above x = 7
+the degenerate root with tail passes is exact.  The fit runs over x in
+[x_lo - 0.05, 7.3].  v follows both ends:
 ln(J_2 - 1) ~ x - ln 8 in the Maxwell-Boltzmann limit, and 3/2 - J_2 ~ x^-2
 toward the degenerate side.  J_2 = f_2^2/(f_1 f_3), with the normalised
 complete Fermi-Dirac integrals f_n(x) = -Li_n(-e^x) taken from mpmath's
@@ -21,11 +22,10 @@ def j2(x):
     return f[1] ** 2 / (f[0] * f[2])
 
 
-def fit(deg: int = 6, samples: int = 600):
+def fit(deg: int = 8, samples: int = 800):
     mp.mp.dps = 30
     x_lo = float(mp.log(mp.e ** mp.mpf("0.1") - 1))  # t = 10: 1/f_1(x) = 10
-    x_hi = float(mp.findroot(lambda x: j2(x) - mp.mpf("1.35"), 4))
-    xs = np.linspace(x_lo - 0.05, x_hi + 0.3, samples)
+    xs = np.linspace(x_lo - 0.05, 7.3, samples)
     J = np.array([float(j2(x)) for x in xs])
     v = np.log((J - 1.0) / (1.5 - J))
     c = np.polyfit(v, xs, deg)
@@ -37,3 +37,5 @@ if __name__ == "__main__":
     c, err = fit()
     print("coefficients (highest degree first):", ", ".join(f"{v:.9e}f" for v in c))
     print(f"max |x_fit - x| = {err:.2e}")
+    mp.mp.dps = 30
+    print(f"3/2 - J_2(7) = {float(1.5 - j2(7)):.9f}")
