@@ -596,18 +596,28 @@ def extras(a, prob, dev_fields, lbm, torch, stream, value, net=None):
     outs = {k: pinned() for k in ("n", "ux", "uy", "T")}
     le = lbm.Lattice([prob], stat="fd", prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05,
                      inv=a.inv, surrogate=net, engine=eng)
+
+    def cycle():
+        lbm.lbm_init_riemann(le.ctx, 0, "field", fields=host)  # host fields -> device inside the call
+        le.step(a.steps)
+        lbm.lbm_moments(le.ctx, 0, **outs)  # device -> host, synchronises
+
+    cycle()  # untimed: the context's one-time staging allocations and step-graph capture
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    lbm.lbm_init_riemann(le.ctx, 0, "field", fields=host)  # host fields -> device inside the call
-    le.step(a.steps)
-    lbm.lbm_moments(le.ctx, 0, **outs)  # device -> host, synchronises
-    el = time.perf_counter() - t0
+    els = []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        cycle()
+        els.append(time.perf_counter() - t0)
     le.close()
+    el = statistics.median(els)
     h2d = 4 * cells * 8
     d2h = 4 * cells * 8
     res["e2e"] = {"value": cells * a.steps / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / a.steps,
                   "d2h_bytes_per_step": d2h / a.steps,
-                  "note": "init from host fields + steps + moments to host, wall clock"}
+                  "cycles_ms": [round(e * 1e3, 2) for e in els],
+                  "note": "median of 5 timed cycles (init from pinned host fields + steps + moments to pinned "
+                          "host arrays, wall clock) after one untimed cycle"}
     # CPU oracle on a bounded sample
     mlups, steps, window, el = oracle_sample_mlups(a.L, a.tau, a.cpu_seconds)
     res["cpu_baseline"] = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
