@@ -121,22 +121,6 @@ __device__ __forceinline__ float j4_degenerate_f(float s) {
          rcp_a((3.0f * s + kPi2f) * (15.0f * s * s + 30.0f * kPi2f * s + 7.0f * kPi2f * kPi2f));
 }
 
-// One fixed-point pass that folds the leading tails into the degenerate
-// root.  With y = e^{-x} the first series terms change f_1, f_2, f_3 by
-// +y, -y, +y, hence J_2 by -J_2 y (2/P_2 + 1/x + 1/P_3); the pass solves the
-// degenerate quadratic for delta minus that change at the current x.  The
-// remaining error is O(y^2): below FP32 resolution of J_4 for x >= 9 after one
-// pass and x >= 7 after two.
-__device__ __forceinline__ float tail_pass_f(float delta, float x) {
-  const float y = expm_a(x);
-  float p2, p3, p4;
-  fd_poly_f(x, p2, p3, p4);
-  const float ip2 = rcp_a(p2), ip3 = rcp_a(p3), ix = rcp_a(x);
-  const float J2d = p2 * p2 * ix * ip3;
-  const float c = J2d * y * (2.0f * ip2 + ix + ip3);
-  return sqrt_a(deg_root_f(delta - c));
-}
-
 // J_4 with the first two series terms of f_2, f_3, f_4 (error O(y^3)).
 __device__ __forceinline__ float j4_tail_f(float x) {
   const float y = expm_a(x);
@@ -166,8 +150,23 @@ __device__ __forceinline__ FD5f fd_eval_deg_f(float x) {
   return r;
 }
 
-// 3/2 - J_2 at x = 7: below it the degenerate root with tail passes is exact.
+// 3/2 - J_2 at x = 7 and at x = 17 (the closed form's threshold).
 constexpr float kDelta7 = 0.078501010f;
+constexpr float kDelta17 = 0.016323599f;
+
+// x for 7 < x < 17 from delta = 3/2 - J_2: a degree-8 polynomial in
+// u = (ln delta - m)/h (u in [-1, 1] over [0.98 delta(17), 1.02 delta(7)]),
+// largest relative error 5.4e-9 (least-squares fit to J_2 = f_2^2/(f_1 f_3)
+// from mpmath's polylogarithm; fit_x_of_j2.py); 1.8e-7 in FP32 evaluation.
+__device__ __forceinline__ float x_degenerate_fit(float delta) {
+  constexpr float c[9] = {-2.114108754e-05f, -5.251981112e-05f, 5.705624853e-05f, -1.250000357e-03f, 1.020720050e-02f,
+                          -1.428147596e-01f, 8.829952733e-01f, -4.990830054e+00f, 1.115240803e+01f};
+  const float u = (__logf(delta) + 3.330093647f) * 1.241846532f;
+  float x = c[0];
+#pragma unroll
+  for (int k = 1; k < 9; ++k) x = fmaf(x, u, c[k]);
+  return x;
+}
 
 // Starting value of the Newton branch (J_2(x_lo) < J_2 <= J_2(7)): x as a
 // degree-8 polynomial in v = ln((J_2 - 1)/(3/2 - J_2)), largest error 4.0e-5
@@ -187,9 +186,10 @@ __device__ __forceinline__ float x_start_general(float J2) {
 // resolution; *xout receives x).
 //  * non-finite input: propagated at once;
 //  * J_2 beyond the clamp interval: x at the nearest end;
-//  * degenerate regime (delta < 3/2 - J_2(7), x > 7): the quadratic root;
-//    closed form J_4 for x >= 17; otherwise one tail pass for x >= 9, two
-//    below;
+//  * x >= 17 (delta <= 3/2 - J_2(17)): the degenerate quadratic root and the
+//    closed-form J_4;
+//  * 7 < x < 17 (delta < 3/2 - J_2(7)): x from the fit x_degenerate_fit
+//    (FP32-exact), J_4 with the first two series terms (error O(e^{-3x}));
 //  * otherwise safeguarded Newton on J_2(x) from the fitted start
 //    x_start_general (within 4e-5), each step one evaluation of f_0..f_4
 //    (three-term series for x >= 4), stopping when the step is below
@@ -212,14 +212,13 @@ __device__ __forceinline__ float j4_from_delta_f(float delta, const InvLimitsF& 
     *xout = L.x_lo;
     return f.f3 * f.f3 * rcp_a(f.f2 * f.f4);
   }
-  if (delta < kDelta7) {
+  if (delta <= kDelta17) {
     const float s = deg_root_f(delta);
-    if (s >= kXDegF * kXDegF) {
-      *xout = sqrt_a(s);
-      return j4_degenerate_f(s);
-    }
-    float x = tail_pass_f(delta, sqrt_a(s));
-    if (x < 9.0f) x = tail_pass_f(delta, x);
+    *xout = sqrt_a(s);
+    return j4_degenerate_f(s);
+  }
+  if (delta < kDelta7) {
+    const float x = x_degenerate_fit(delta);
     *xout = x;
     return j4_tail_f(x);
   }

@@ -10,8 +10,11 @@ toward the degenerate side.  J_2 = f_2^2/(f_1 f_3), with the normalised
 complete Fermi-Dirac integrals f_n(x) = -Li_n(-e^x) taken from mpmath's
 polylogarithm (independent of the library and of the test oracle).
 
+A second fit (fit_degenerate) gives x directly for 7 < x < 17 from
+ln(3/2 - J_2), in place of the tail passes.
+
 Run: python paper_1510_07328_gb300/fit_x_of_j2.py  (prints the coefficients,
-highest degree first, and the largest error of the fit in x).
+highest degree first, and the largest errors of the fits).
 """
 import mpmath as mp
 import numpy as np
@@ -33,9 +36,30 @@ def fit(deg: int = 8, samples: int = 800):
     return c, err
 
 
+def fit_degenerate(deg: int = 8, samples: int = 700):
+    """x for 7 < x < 17 (delta = 3/2 - J_2 between delta(17) and delta(7)) as a
+    degree-8 polynomial in u = (ln delta - m)/h, u in [-1, 1] over
+    [0.98 delta(17), 1.02 delta(7)]; fitted over x in [6.95, 17.1].  The
+    inversion uses it in place of the tail passes.  Returns (coefficients,
+    m, h, largest relative error, delta(7), delta(17))."""
+    mp.mp.dps = 30
+    d7, d17 = float(1.5 - j2(7)), float(1.5 - j2(17))
+    xs = np.linspace(6.95, 17.1, samples)
+    d = np.array([float(1.5 - j2(x)) for x in xs])
+    lo, hi = np.log(d17 * 0.98), np.log(d7 * 1.02)
+    m, h = 0.5 * (lo + hi), 0.5 * (hi - lo)
+    u = (np.log(d) - m) / h
+    c = np.polyfit(u, xs, deg)
+    err = float((np.abs(np.polyval(c, u) - xs) / xs).max())
+    return c, m, h, err, d7, d17
+
+
 if __name__ == "__main__":
     c, err = fit()
     print("coefficients (highest degree first):", ", ".join(f"{v:.9e}f" for v in c))
     print(f"max |x_fit - x| = {err:.2e}")
     mp.mp.dps = 30
     print(f"3/2 - J_2(7) = {float(1.5 - j2(7)):.9f}")
+    c, m, h, err, d7, d17 = fit_degenerate()
+    print("degenerate-range coefficients:", ", ".join(f"{v:.9e}f" for v in c))
+    print(f"m = {m:.9f}, 1/h = {1.0 / h:.9f}, max relative error {err:.2e}, 3/2 - J_2(17) = {d17:.9f}")
