@@ -21,7 +21,7 @@ full index tensors (no closed-form shortcuts):
   Eq. (expansao0) evaluated at the lattice nodes ``xi_a = c_0 e_a``,
   ``c_0 = sqrt(3 I_4/I_2)``.
 
-Readings of garbled or ambiguous passages (listed again in the design doc):
+Readings of garbled or ambiguous passages:
 
 * ``Delta_L`` is the positive square root of ``Delta_L^2``.
 * ``c'_1 = cbar_1 = 0`` (Eq. (H1) has no lower-order part).
