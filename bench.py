@@ -131,7 +131,7 @@ def workload_config(a, world, probs=None, tiling=None):
                     "t0": "d2v9 K=3 generalized-polynomial LBGK, theta = 0 closure (constant J)",
                     "mb": "d2v9 K=3 LBGK, Maxwell-Boltzmann limit (J = 1)"}[a.stat],
         "storage": {"f32": "FP32 deviations g = f - W_ref", "bf16": "BF16 deviations", "f64": "FP64 f"}[a.prec],
-        "inversion": "exact (closed-form degenerate root, tail passes, Newton)" if a.inv == "exact"
+        "inversion": "exact (closed-form degenerate root for x >= 17, fitted x(delta) for 7 < x < 17, one Newton step from a fitted start below)" if a.inv == "exact"
         else "learned network 2-64-64-2 (%s) + one third-order polish + residual check, exact fallback"
         % {"tensor": "tcgen05 MMAs over 128-cell tile rows", "mma": "warp-level MMAs, activations in registers",
            "fp32": "FP32 pipe"}[a.engine],
