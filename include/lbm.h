@@ -246,8 +246,9 @@ int64_t lbm_launch_count(const lbm_ctx* ctx);
  *             W3 [2][64], b3 [2] (row-major [out][in]): 4482 values.
  * A context created with inv = LBM_INV_SURROGATE (FD statistics, FP32 or BF16
  * storage) evaluates the network per cell inside the step, polishes x = mu/T
- * by one Newton step on J_2(x) and falls back to the exact inversion when that
- * step is not below 5e-4 x. */
+ * by one third-order step on J_2(x) = J_2 and falls back to the exact
+ * inversion when the first-order step is not below 2.5e-2 max(|x|, 1)
+ * (see lbm_surrogate_engine). */
 #define LBM_SURROGATE_NPARAM 4482
 
 typedef struct {
