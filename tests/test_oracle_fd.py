@@ -113,3 +113,30 @@ def test_fd_values_degenerate_quadratic():
     s = x * x
     delta = math.pi ** 2 * (3 * s - math.pi ** 2) / (6 * s * (s + math.pi ** 2))
     np.testing.assert_allclose(1.5 - fd.j2_of_x(x), delta, rtol=1e-9)
+
+
+@pytest.mark.parametrize("t", [0.005, 0.05, 0.1, 0.2, 0.3])
+def test_inversion_at_reference_states(t):
+    """The inversion end to end at the states used across the workloads:
+    x(t), J_2(x) and J_4(x) against mpmath's polylogarithm (solved
+    independently), and the oracle's J_2 -> x bisection recovering x."""
+    mp = pytest.importorskip("mpmath")
+    from oracle import lbm as olbm
+
+    mp.mp.dps = 40
+
+    def f(n, x):
+        return -mp.polylog(n, -mp.e ** x)
+
+    x_ref = mp.findroot(lambda x: 1 / f(1, x) - t, 1 / mp.mpf(t))
+    j2_ref = f(2, x_ref) ** 2 / (f(1, x_ref) * f(3, x_ref))
+    j4_ref = f(3, x_ref) ** 2 / (f(2, x_ref) * f(4, x_ref))
+    x = float(fd.x_of_t(np.array([t]))[0])
+    assert abs(x - float(x_ref)) <= 1e-13 * abs(float(x_ref))
+    assert abs(float(fd.j2_of_x(np.array([x]))[0]) - float(j2_ref)) <= 1e-14
+    assert abs(float(fd.j4_of_x(np.array([x]))[0]) - float(j4_ref)) <= 1e-14
+    x_back = float(olbm.invert_j2(np.array([float(j2_ref)]))[0])
+    # J_2 is flat in x as t -> 0 (3/2 - J_2 ~ x^-2): the round trip's x error
+    # is the FP64 rounding of J_2 divided by dJ_2/dx
+    dj2 = 2 * (1.5 - float(j2_ref)) / float(x_ref)
+    assert abs(x_back - float(x_ref)) <= 4 * 2.2e-16 * 1.5 / dj2 + 1e-12 * abs(float(x_ref))
