@@ -37,3 +37,18 @@ def test_oracle_sample_takes_a_finite_step(workload):
     assert g.shape == f.shape and np.isfinite(g).all()
     # one collision conserves the mass of the sample (periodic wrap)
     assert abs(g.sum() - f.sum()) < 1e-12 * abs(f.sum())
+
+
+@pytest.mark.parametrize("workload", ["smooth_t", "batched", "d1v3", "porous"])
+def test_workload_config_carries_the_contract_keys(workload):
+    """Every workload's config names the workload, states how L2 is handled
+    between steps, and the parallelism."""
+    from paper_1510_07328_gb300 import inputs
+
+    a = args(workload)
+    bench.settle_closure(a)
+    probs = inputs.batched(count=4) if workload == "batched" else None
+    cfg = bench.workload_config(a, 1, probs)
+    assert cfg["workload"].startswith(workload.split("_")[0])
+    assert "L2" in cfg["l2"] and cfg["parallelism"] == "single GPU"
+    assert bench.workload_config(a, 2, probs)["parallelism"] == "replicas x2"
