@@ -148,15 +148,26 @@ def _ptr(a) -> int | None:
 # ---------------------------------------------------------------- C-ABI calls, same names
 
 
+def _choice(kind: str, value, table: dict):
+    if value not in table:
+        raise ValueError(f"unknown {kind} {value!r}; expected one of {sorted(table)}")
+    return table[value]
+
+
 def lbm_create(problems, stat="fd", prec="f64", inv="exact", stream=None, dim=2):
     """problems: list of dicts with nx, ny, tau, bc_x, bc_y, n_ref, t_ref;
     dim 2: d2v9, dim 1: d1v3 (ny = 1)."""
+    stat_c = _choice("closure", stat, STAT)
+    prec_c = _choice("storage", prec, PREC)
+    inv_c = _choice("inversion", inv, {"exact": LBM_INV_EXACT, "surrogate": LBM_INV_SURROGATE})
+    for p in problems:
+        for k in ("bc_x", "bc_y"):
+            _choice("boundary", p.get(k, "periodic"), BC)
     arr = (lbm_problem * len(problems))()
     for i, p in enumerate(problems):
         arr[i] = lbm_problem(int(p["nx"]), int(p["ny"]), float(p["tau"]), BC[p.get("bc_x", "periodic")],
                              BC[p.get("bc_y", "periodic")], float(p.get("n_ref", 1.0)), float(p.get("t_ref", 0.05)))
-    par = lbm_params(int(dim), 3, STAT[stat], PREC[prec], LBM_INV_EXACT if inv == "exact" else LBM_INV_SURROGATE,
-                     len(problems), arr)
+    par = lbm_params(int(dim), 3, stat_c, prec_c, inv_c, len(problems), arr)
     ctx = C.c_void_p()
     _check(LIB.lbm_create(C.byref(par), C.c_void_p(stream or 0), C.byref(ctx)), None)
     return ctx

@@ -128,3 +128,18 @@ def test_create_rejects_d1v3_misuse(lib):
     assert "ny = 1" in lib.lbm_last_error(None)
     par = lib.lbm_params(0, 3, lib.STAT["t0"], 0, 0, 1, arr)
     assert lib.LIB.lbm_create(C.byref(par), None, C.byref(ctx)) == lib.LBM_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(stat="FD"), "closure"),
+    (dict(prec="fp32"), "storage"),
+    (dict(inv="Exact"), "inversion"),   # must not fall through to the learned inversion
+])
+def test_binding_rejects_unknown_names(lib, kw, msg):
+    p = dict(nx=8, ny=4, tau=0.8, bc_x="periodic", bc_y="periodic", n_ref=1.0, t_ref=0.05)
+    with pytest.raises(ValueError, match=msg):
+        lib.lbm_create([p], **kw)
+    with pytest.raises(ValueError, match="boundary"):
+        lib.lbm_create([dict(p, bc_x="wall")])
+    with pytest.raises(ValueError, match="engine"):
+        lib.lbm_surrogate_engine(None, "tcgen05")
