@@ -50,3 +50,25 @@ def test_replicas_max_time_over_two_ranks():
     assert out[0][0] == 2 and out[1][0] == 2
     assert out[0][1] == out[1][1] == 3.5  # max of 1.0 and 3.5 ms
     assert abs(out[0][2] - 2 * 1000 * 10 / 3.5e-3 / 1e6) < 1e-9
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """bench.py --impl reference launched as the contract launches N > 1
+    (torchrun, two ranks, 127.0.0.1): rank 0 alone times the oracle and prints
+    one JSON line; the other rank exits 0 without work."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
+           os.path.join(root, "bench.py"), "--impl", "reference", "--gpus", "2", "--L", "64", "--steps", "1",
+           "--warmup", "0"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
