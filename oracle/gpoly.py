@@ -24,6 +24,13 @@ full index tensors (no closed-form shortcuts):
 Readings of garbled or ambiguous passages:
 
 * ``Delta_L`` is the positive square root of ``Delta_L^2``.
+* The polynomials, and with them the expansion, exist only where every
+  ``Delta_L^2`` used is positive and finite and ``c_0^2 = 3 I_4/I_2`` is
+  positive.  For the K = 3 equilibrium built from moments with ratios J_2 and
+  J_4 this is 0 < J_2 < 2 and J_4 < 3/2 (D = 2).  A state outside (reachable
+  only through measured moments, never from an FD weight) has no real
+  polynomials: ``equilibrium`` returns NaN for it, explicitly, and
+  ``in_expansion_domain`` says which states those are.
 * ``c'_1 = cbar_1 = 0`` (Eq. (H1) has no lower-order part).
 * The constant ``c_0`` of Eq. (H0) is ``c_{K=0} = I_0^{-1/2}``; the velocity
   scale of the lattice is the separate ``c_0 = sqrt(3 I_4/I_2)``.
@@ -117,6 +124,26 @@ def Delta2(I: dict, L: int, D: int):
     return 2.0 / ((D + L) - J(I, L) * (D + L - 2))
 
 
+def sqrt_domain(d2):
+    """Delta_L = +sqrt(Delta_L^2) where Delta_L^2 is positive and finite; NaN
+    where it is not (no real polynomial exists there), without a warning."""
+    d2 = np.asarray(d2, dtype=np.float64)
+    ok = np.isfinite(d2) & (d2 > 0.0)
+    return np.sqrt(np.where(ok, d2, 1.0)) * np.where(ok, 1.0, np.nan)
+
+
+def in_expansion_domain(I: dict, D: int, kmax: int = 3):
+    """True where the K = kmax expansion exists: Delta_2^2 .. Delta_{2 kmax - 2}^2
+    positive and finite, and I_4/I_2 > 0 (a real lattice scale c_0)."""
+    ok = np.ones(np.shape(I[0]), dtype=bool)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        for K in range(2, kmax + 1):
+            d2 = Delta2(I, 2 * K - 2, D)
+            ok &= np.isfinite(d2) & (d2 > 0.0)
+        ok &= np.asarray(I[4] / I[2]) > 0.0
+    return ok
+
+
 def small_delta(I: dict, L: int, D: int):
     """delta_L = 2 I_{L+2} I_{L-2} / Delta_L^2."""
     return 2.0 * I[L + 2] * I[L - 2] / Delta2(I, L, D)
@@ -129,11 +156,12 @@ def coefficients(I: dict, D: int, kmax: int = 3, d4_sign: float = 1.0) -> dict:
     """c_K, c'_K, cbar_K (K <= kmax) and, for kmax = 4, d_4, d'_4, dbar_4."""
     c = {}
     for K in range(kmax + 1):
-        c[("c", K)] = 1.0 / np.sqrt(I[2 * K])
+        c[("c", K)] = 1.0 / sqrt_domain(I[2 * K])
     c[("cp", 1)] = 0.0 * c[("c", 1)]
     c[("cb", 1)] = 0.0 * c[("c", 1)]
     for K in range(2, kmax + 1):
-        Dl = np.sqrt(Delta2(I, 2 * K - 2, D))
+        with np.errstate(divide="ignore"):
+            Dl = sqrt_domain(Delta2(I, 2 * K - 2, D))
         c[("cp", K)] = -c[("c", K)] * (I[2 * K - 2] / I[2 * K - 4]) * Dl
         c[("cb", K)] = c[("c", K)] * (Dl - 1.0) / (D + 2 * K - 4)
     if kmax >= 4:
@@ -263,7 +291,7 @@ def equilibrium(I: dict, u0: np.ndarray, D: int) -> np.ndarray:
     """
     e, _ = lattice(D)
     coef = coefficients(I, D, kmax=3)
-    c0 = np.sqrt(3.0 * I[4] / I[2])  # (C,)
+    c0 = sqrt_domain(3.0 * I[4] / I[2])  # (C,); NaN outside the expansion's domain
     u = c0[:, None] * np.asarray(u0, dtype=np.float64)
     xi = c0[:, None, None] * e[None, :, :]  # (C, Q, D)
     # broadcast coefficients over the velocity axis
@@ -275,7 +303,10 @@ def equilibrium(I: dict, u0: np.ndarray, D: int) -> np.ndarray:
     S = S + 0.5 * np.einsum("cij,cqij->cq", A[2], P[2])
     S = S + (1.0 / 6.0) * np.einsum("cijk,cqijk->cq", A[3], P[3])
     w = weights(D, I[0], J(I, 2))
-    return w * S
+    out = w * S
+    # a state outside the domain gets NaN in every population, explicitly
+    out[~in_expansion_domain(I, D, kmax=3)] = np.nan
+    return out
 
 
 def feq_closed_form(n, u0, J2, J4, D: int) -> np.ndarray:

@@ -115,7 +115,7 @@ __device__ __forceinline__ void relax_store_dev(const ProbDev& P, const float g[
     dWl = dn * J2 / 36.0f;
   }
   const float W0 = P.f.wref[0] + dW0, Ws = P.f.wref[1] + dWs, Wl = P.f.wref[2] + dWl;
-  const float D22 = __fdividef(1.0f, 2.0f - J2);
+  const float D22 = delta22_f(J2);  // NaN outside 0 < J_2 < 2
   const float D42 = __fdividef(1.0f, 3.0f - 2.0f * J4);
   const float iJ2 = __fdividef(1.0f, J2);
   // The bracket's constants, with t = J_4 Delta_4^2 and P = (1 - J_2) t:

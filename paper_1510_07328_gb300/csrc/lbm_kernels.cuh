@@ -44,6 +44,19 @@ struct FixedJ {
   static constexpr double j4 = STAT == STAT_T0 ? 4.0 / 3.0 : 1.0;
 };
 
+// Delta_2^2 = 2/((D+2) - J_2 D) = 1/(2 - J_2) for D = 2 (definitions under
+// Eq. (H4)).  The polynomials need Delta_2 = +sqrt(Delta_2^2) real and the
+// lattice scale c_0^2 = 3 I_4/I_2 = 3 I_2/(I_0 J_2) positive, so the K = 3
+// equilibrium exists for 0 < J_2 < 2 only.  Outside (reachable only through
+// measured moments) there is no equilibrium: NaN is returned, and every
+// population of the cell becomes NaN (counted as non-finite by lbm_moments).
+__device__ __forceinline__ double delta22(double J2) {
+  return (J2 > 0.0 && J2 < 2.0) ? 1.0 / (2.0 - J2) : __longlong_as_double(0x7ff8000000000000ll);
+}
+__device__ __forceinline__ float delta22_f(float J2) {
+  return (J2 > 0.0f && J2 < 2.0f) ? __fdividef(1.0f, 2.0f - J2) : __int_as_float(0x7fc00000);
+}
+
 // Locate the problem and the (row, x-tile) of this CTA.
 __device__ __forceinline__ int find_problem(const ProbDev* __restrict__ probs, int nprob, int64_t tile) {
   int lo = 0, hi = nprob - 1;
@@ -58,7 +71,7 @@ __device__ __forceinline__ int find_problem(const ProbDev* __restrict__ probs, i
 // D = 2), FP64.  W_0 = n(1 - 5J_2/9), W_short = nJ_2/9, W_long = nJ_2/36.
 __device__ __forceinline__ void feq_f64(double n, double ux, double uy, double J2, double J4, double fe[9]) {
   const double u2 = ux * ux + uy * uy;
-  const double D22 = 1.0 / (2.0 - J2);        // 2/((D+2) - J_2 D)
+  const double D22 = delta22(J2);             // 2/((D+2) - J_2 D), NaN outside 0 < J_2 < 2
   const double D42 = 1.0 / (3.0 - 2.0 * J4);  // 2/((D+4) - J_4 (D+2))
   const double iJ2 = 1.0 / J2;
   const double a1 = 3.0 * iJ2, a2 = 4.5 * iJ2, b0 = 1.5 * iJ2;

@@ -84,7 +84,7 @@ __device__ __forceinline__ void relax_force_store_dev(const ProbDev& P, const fl
     dWl = dn * J2 / 36.0f;
   }
   const float W0 = P.f.wref[0] + dW0, Ws = P.f.wref[1] + dWs, Wl = P.f.wref[2] + dWl;
-  const float D22 = __fdividef(1.0f, 2.0f - J2);
+  const float D22 = delta22_f(J2);  // NaN outside 0 < J_2 < 2
   const float D42 = __fdividef(1.0f, 3.0f - 2.0f * J4);
   const float iJ2 = __fdividef(1.0f, J2);
   const float t = J4 * D42, Pt = (1.0f - J2) * t;

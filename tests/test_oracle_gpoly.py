@@ -272,3 +272,43 @@ def test_zero_temperature_velocity_scale():
         I = g.moments_t0(mu, Dd, nmax=3)
         assert abs(math.sqrt(3 * I[4] / I[2]) - math.sqrt(6 * mu / (Dd + 4))) < 1e-15
         assert abs(I[0] - (2 * math.pi * mu) ** (Dd / 2) / math.gamma(Dd / 2 + 1)) < 1e-15
+
+
+def test_expansion_domain_is_where_delta2_is_positive():
+    """The polynomials need Delta_L = +sqrt(Delta_L^2) real (definitions under
+    Eq. (H4)) and a real lattice scale c_0 = sqrt(3 I_4/I_2) (Sect. "The
+    Gaussian quadrature").  With I_4 = I_2^2/(I_0 J_2), Delta_2^2 = 1/(2 - J_2)
+    for D = 2, so the K = 3 equilibrium exists for 0 < J_2 < 2 only.  Inside:
+    every coefficient and population is finite over the FD range the tests and
+    workloads use; outside: every population is NaN, set explicitly (no
+    floating-point warning is raised on the way)."""
+    import warnings
+
+    from oracle import lbm as olbm
+
+    rng = np.random.default_rng(7)
+    with warnings.catch_warnings():
+        warnings.simplefilter("error")
+        # FD states: n in [0.5, 2], t from the clamp's low end to its high end
+        for t in (1e-3, 5e-3, 0.02, 0.05, 0.1, 0.3, 1.0, 10.0):
+            n = rng.uniform(0.5, 2.0, 16)
+            x = fd.x_of_t(np.full(16, t))
+            j2 = fd.j2_of_x(x)
+            I = olbm.moment_set(n, j2, fd.j4_of_x(x), "fd", x)
+            coef = g.coefficients(I, D, kmax=3)
+            assert all(np.isfinite(v).all() for v in coef.values())
+            assert g.in_expansion_domain(I, D).all()
+            u0 = rng.uniform(-0.3, 0.3, (16, 2))
+            assert np.isfinite(g.equilibrium(I, u0, D)).all()
+        # measured J_2 on either side of the boundaries (x of a mid-range FD state)
+        x = fd.x_of_t(np.full(6, 0.05))
+        j2 = np.array([1.999, 1.9, 2.0, 2.3, 5.0, -0.1])
+        I = olbm.moment_set(np.ones(6), j2, fd.j4_of_x(x), "fd", x)
+        feq = g.equilibrium(I, np.full((6, 2), 0.01), D)
+    inside = np.array([True, True, False, False, False, False])
+    assert np.array_equal(g.in_expansion_domain(I, D), inside)
+    assert np.isfinite(feq[inside]).all()
+    assert np.isnan(feq[~inside]).all()
+    # just inside, the tensor form still equals the printed closed form
+    ref = g.feq_closed_form(np.ones(2), np.full((2, 2), 0.01), j2[:2], fd.j4_of_x(x[:2]), D)
+    np.testing.assert_allclose(feq[:2], ref, rtol=1e-12, atol=0)
