@@ -29,7 +29,7 @@
  *    a call that writes host memory synchronises that stream before it returns.
  *  - Every call returns an lbm_status; nothing aborts or throws.  On failure
  *    lbm_last_error() returns a message (per context; lbm_last_error(NULL)
- *    gives the last failure of lbm_create).  An asynchronous CUDA error
+ *    gives the last failure of a call without a context).  An asynchronous CUDA error
  *    surfaces at the next call that synchronises (LBM_ECUDA).
  *  - Pointers are plain host or device addresses as stated per argument; the
  *    library never frees memory it did not allocate.
@@ -223,8 +223,9 @@ lbm_status lbm_set_force(lbm_ctx* ctx, int32_t problem, double fx, double fy);
 /* Release everything the context owns (synchronises its stream first). */
 lbm_status lbm_destroy(lbm_ctx* ctx);
 
-/* Message of the last failure on ctx (or of lbm_create if ctx is NULL);
- * valid until the next call on the same context. */
+/* Message of the last failure on ctx; with ctx NULL, of the last failure of a
+ * call without a context (lbm_create, lbm_conservation_sums_static).  Valid
+ * until the next call on the same context (or the next context-free call). */
 const char* lbm_last_error(const lbm_ctx* ctx);
 
 /* Number of kernel launches issued by the library on this context since it
@@ -314,10 +315,24 @@ lbm_status lbm_surrogate_engine(lbm_ctx* ctx, int32_t engine);
 
 /* Cells that went through the network (finite J_2 inside the clamp
  * interval), and those of them that fell back to the exact inversion, since
- * the context was created.  Synchronises.  Returns
- * LBM_ETIMEOUT (counts still filled) if a tensor-core wait ever gave up; the
- * cells concerned were served by the exact inversion. */
+ * the context was created.  Synchronises.  Returns LBM_ETIMEOUT (counts still
+ * filled) if a tensor-core wait ever gave up.  After a wait between layers
+ * gave up, the CTA concerned served its remaining cells by the exact
+ * inversion: the results stand.  If the wait for the last MMA before tensor
+ * memory is freed also gave up (the message says so), tensor memory was
+ * released while an MMA may still have been writing it, and the results of
+ * the context's steps are not to be trusted. */
 lbm_status lbm_surrogate_stats(lbm_ctx* ctx, int64_t* fallbacks, int64_t* evaluations);
+
+/* The tensor-core engine's limit on the polls of each wait between its
+ * layers (an mbarrier that the MMAs complete): polls >= 0 sets it, polls < 0
+ * restores the default (4,194,304).  A wait that reaches the limit gives up
+ * for its CTA as described under lbm_surrogate_stats; 0 makes every such wait
+ * give up at once, which is how the recovery path is tested.  The final wait
+ * before tensor memory is freed keeps the default limit.  The paper has no
+ * counterpart (failure handling of this implementation).  Drops captured
+ * graphs.  Errors: LBM_EINVAL (NULL context). */
+lbm_status lbm_surrogate_wait_limit(lbm_ctx* ctx, int32_t polls);
 
 /* lbm_conservation_sums_static - the paper has no counterpart to this call;
  * it exists for callers that cannot allocate device memory.
@@ -327,31 +342,43 @@ lbm_status lbm_surrogate_stats(lbm_ctx* ctx, int64_t* fallbacks, int64_t* evalua
  * allocator or an arena sized at start-up), or a loop that must not allocate
  * while it runs.  lbm_moments allocates its per-block partial sums on first
  * use; this call computes the same conservation totals with its partial sums
- * in a fixed file-scope device array instead, and allocates nothing.
+ * in a fixed file-scope device array instead, and allocates nothing, on the
+ * device or the host (its error message goes to a fixed buffer).
  *
  * f:     device pointer, FP64 populations [9][ny][nx] (the layout that
  *        lbm_get_populations writes), read only.
- * stat:  lbm_stat; for LBM_STAT_FD the count of clamped inversions is formed
- *        as in lbm_moments, otherwise it is 0.
+ * solid: device pointer to one byte per cell [ny][nx], nonzero for an
+ *        obstacle cell (the mask given to lbm_set_obstacles), or NULL for
+ *        none.  Obstacle cells are left out of every total, as lbm_moments
+ *        leaves them out.
+ * stat:  lbm_stat; for LBM_STAT_FD a cell counts as clamped when its finite
+ *        J_2 lies outside the inversion's interval, the rule of lbm_moments;
+ *        otherwise the count is 0.
  * out:   device pointer to 6 doubles, written in stream order: sum n,
  *        sum j_x, sum j_y, sum E, clamped count, non-finite count (the fields
  *        of lbm_diag).
  * cuda_stream: cudaStream_t for the launches (NULL = legacy default stream).
  *
  * Limit: nx * ny <= LBM_STATIC_SUMS_MAX_CELLS (16,777,216 cells, a 4096 x 4096
- * lattice); larger sizes return LBM_EINVAL before any GPU work.  The scratch
- * array (192 KiB) lives on every GPU that loads the library until the process
- * exits.  The first call on each device looks up the array's device address
- * with cudaGetSymbolAddress and runs a one-thread set-up kernel, synchronising
- * the stream; make that first call before any stream capture.  All calls
- * share the array: calls whose kernels may overlap on the GPU (different
- * streams or host threads) race and must be serialised by the caller.
- * Asynchronous after the first call.  Errors: LBM_EINVAL (NULL pointer,
- * nx or ny < 1, size above the limit, bad stat), LBM_EUNSUPPORTED (device
- * index >= 64), LBM_ECUDA (set-up or launch failed).  No message is stored. */
+ * lattice); larger sizes return LBM_EINVAL before any GPU work, with a message
+ * in lbm_last_error(NULL).  The limit is a policy that bounds the work of one
+ * call, not the capacity of the scratch array (the kernel is a grid-stride
+ * loop over at most 4096 blocks, so the array would serve any size).  The
+ * scratch array (192 KiB) lives on every GPU that loads the library until the
+ * process exits.  The first call on each device looks up the array's device
+ * address with cudaGetSymbolAddress and runs a one-thread set-up kernel,
+ * synchronising the stream; make that first call before any stream capture.
+ * The looked-up address is kept per device index for the life of the
+ * process: after cudaDeviceReset it is stale, so do not call this entry point
+ * again on a device that was reset.  All calls share the array: calls whose
+ * kernels may overlap on the GPU (different streams or host threads) race and
+ * must be serialised by the caller.  Asynchronous after the first call.
+ * Errors (message in lbm_last_error(NULL)): LBM_EINVAL (NULL f or out, nx or
+ * ny < 1, size above the limit, bad stat), LBM_EUNSUPPORTED (device index
+ * >= 64), LBM_ECUDA (set-up or launch failed). */
 #define LBM_STATIC_SUMS_MAX_CELLS 16777216
-lbm_status lbm_conservation_sums_static(const double* f, int32_t nx, int32_t ny, int32_t stat, double* out,
-                                        void* cuda_stream);
+lbm_status lbm_conservation_sums_static(const double* f, int32_t nx, int32_t ny, const uint8_t* solid, int32_t stat,
+                                        double* out, void* cuda_stream);
 
 #ifdef __cplusplus
 }

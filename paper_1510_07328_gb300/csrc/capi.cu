@@ -23,6 +23,9 @@ using namespace lbm;
 namespace {
 
 constexpr int kGraphChunk = 16;  // steps per captured graph (even: buffers return)
+// counters of a learned-inversion context: fallbacks, evaluations, tensor-core
+// round timeouts, timeouts of the final wait before tensor memory is freed
+constexpr int kNSurrCounters = 4;
 
 // ------------------------------------------------------------------ per-context setup
 
@@ -100,7 +103,7 @@ static __global__ void __launch_bounds__(256) reduce_partials_kernel(const doubl
 
 
 std::mutex g_err_mu;
-std::string g_create_err;
+char g_create_err[512] = "";  // last context-free failure (fixed buffer: no allocation)
 
 size_t elem_size(int prec) { return prec == LBM_F64 ? 8 : prec == LBM_F32_DEV ? 4 : 2; }
 
@@ -133,7 +136,9 @@ struct lbm_ctx {
   int64_t launches = 0;
   std::string err;
   MlpParams* surr = nullptr;               // host copy of the network (learned inversion)
-  unsigned long long* surr_count = nullptr;  // device: fallbacks, evaluations, tensor-core timeouts
+  unsigned long long* surr_count = nullptr;  // device: fallbacks, evaluations, tensor-core round timeouts,
+                                             // timeouts of the final wait before TMEM is freed
+  int tc_polls = kTcWaitPolls;               // per-round poll limit of the tensor-core engine
   void* wtc = nullptr;                       // device: the network's FP16 tensor-core operands (kTcBytes)
   void* wmm = nullptr;                       // device: the network's warp-MMA fragments (kMmBytes)
   int surr_engine = LBM_SURROGATE_TENSOR_CORES;
@@ -148,7 +153,7 @@ lbm_status fail(lbm_ctx* ctx, lbm_status s, const std::string& m) {
     ctx->err = m;
   } else {
     std::lock_guard<std::mutex> g(g_err_mu);
-    g_create_err = m;
+    std::snprintf(g_create_err, sizeof(g_create_err), "%s", m.c_str());
   }
   return s;
 }
@@ -168,7 +173,7 @@ lbm_status fail(lbm_ctx* ctx, lbm_status s, const std::string& m) {
 unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 void launch_step(lbm_ctx* c, const void* in, void* out, cudaStream_t s) {
-  StepArgs a{in, out, c->pd, c->nprob, (int)c->ntiles, c->plane, c->lim, c->limf};
+  StepArgs a{in, out, c->pd, c->nprob, (int)c->ntiles, c->plane, c->lim, c->limf, c->tc_polls};
   const unsigned grid = c->ctas > 0 ? (unsigned)std::min<int64_t>(c->ctas, c->ntiles) : (unsigned)c->ntiles;
   if (c->dim == 1) {
     launch_step_d1(c->prec, c->stat, grid, s, a);
@@ -270,12 +275,21 @@ bool valid_t(double t) { return t >= kTMin && t <= kTMax; }
 
 }  // namespace
 
+namespace lbm {
+// Stores the message lbm_last_error(NULL) returns, for context-free calls;
+// copies into a fixed buffer (allocates nothing).
+void set_global_error(const char* m) {
+  std::lock_guard<std::mutex> g(g_err_mu);
+  std::snprintf(g_create_err, sizeof(g_create_err), "%s", m);
+}
+}  // namespace lbm
+
 extern "C" {
 
 const char* lbm_last_error(const lbm_ctx* ctx) {
   if (ctx) return ctx->err.c_str();
   std::lock_guard<std::mutex> g(g_err_mu);
-  return g_create_err.c_str();
+  return g_create_err;
 }
 
 int64_t lbm_launch_count(const lbm_ctx* ctx) { return ctx ? ctx->launches : 0; }
@@ -362,8 +376,8 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&ctx->lim_d, sizeof(InvLimits));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->diag_d, sizeof(double) * kNPartial);
   if (e == cudaSuccess && p->inv == LBM_INV_SURROGATE) {
-    e = cudaMalloc(&ctx->surr_count, 3 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->surr_count, 0, 3 * sizeof(unsigned long long), ctx->stream);
+    e = cudaMalloc(&ctx->surr_count, kNSurrCounters * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->surr_count, 0, kNSurrCounters * sizeof(unsigned long long), ctx->stream);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->wtc, kTcBytes);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->wmm, kMmBytes);
     if (e == cudaSuccess) {
@@ -651,12 +665,23 @@ lbm_status lbm_surrogate_engine(lbm_ctx* ctx, int32_t engine) {
 lbm_status lbm_surrogate_stats(lbm_ctx* ctx, int64_t* fallbacks, int64_t* evaluations) {
   if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_surrogate_stats: NULL context");
   if (!ctx->surr_count) return fail(ctx, LBM_EINVAL, "lbm_surrogate_stats: not a learned-inversion context");
-  unsigned long long h[3] = {0, 0, 0};
+  unsigned long long h[kNSurrCounters] = {0, 0, 0, 0};
   CK(cudaMemcpyAsync(h, ctx->surr_count, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   if (fallbacks) *fallbacks = (int64_t)h[0];
   if (evaluations) *evaluations = (int64_t)h[1];
+  if (h[3])
+    return fail(ctx, LBM_ETIMEOUT,
+                "lbm_surrogate_stats: a tensor-core wait before freeing tensor memory timed out; the results of "
+                "the steps since the context was created are not trusted");
   if (h[2]) return fail(ctx, LBM_ETIMEOUT, "lbm_surrogate_stats: a tensor-core wait timed out (cells served exactly)");
+  return LBM_OK;
+}
+
+lbm_status lbm_surrogate_wait_limit(lbm_ctx* ctx, int32_t polls) {
+  if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_surrogate_wait_limit: NULL context");
+  ctx->tc_polls = polls < 0 ? kTcWaitPolls : (int)polls;
+  drop_graphs(ctx);
   return LBM_OK;
 }
 

@@ -10,6 +10,11 @@
 
 namespace lbm {
 
+// Polls of an mbarrier wait of the tensor-core engine before it counts as
+// failed (per layer round; the wait at the end of the kernel always uses this
+// full limit).
+constexpr int kTcWaitPolls = 1 << 22;
+
 struct StepArgs {
   const void* in;
   void* out;
@@ -19,6 +24,7 @@ struct StepArgs {
   int64_t plane;
   InvLimits lim;
   InvLimitsF limf;
+  int tc_polls;  // per-round poll limit of the tensor-core engine (lbm_surrogate_wait_limit)
 };
 
 struct MlpParams;

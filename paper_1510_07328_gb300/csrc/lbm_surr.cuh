@@ -142,8 +142,6 @@ __global__ void __launch_bounds__(kTileX) stream_collide_surr(const T* __restric
   flush_counts(nfb, nev, counters);
 }
 
-// Polls per mbarrier wait before a tensor-core round counts as failed.
-constexpr int kTcSpin = 1 << 22;
 
 // Tile rows per tensor-core round.  Two rows per round (two independent MMA
 // chains in flight) need 128 TMEM columns, 74 KB of shared memory and about
@@ -240,17 +238,20 @@ __device__ __forceinline__ float stage_pop(const unsigned char* st, int a, uint3
 //     y = D[0..1] + D[2..3];
 //  4. the polish, the residual check and the relaxation per cell, with the
 //     populations read again from the stage.
-// The issuing thread alone waits on the mbarrier (bounded); a barrier with a
-// reduction (bar.red.or) then releases the CTA with the outcome, so the other
-// warps spend no issue slots on polling.  A CTA whose wait ran out counts the
-// event in counters[2], serves its remaining cells with the exact inversion,
-// waits (bounded) for its last MMA and still frees its TMEM.  The persistent
+// The issuing thread alone waits on the mbarrier, at most `polls` polls per
+// round; a barrier with a reduction (bar.red.or) then releases the CTA with
+// the outcome, so the other warps spend no issue slots on polling.  A CTA
+// whose wait ran out counts the event in counters[2] and serves its remaining
+// cells with the exact inversion.  Before it frees its TMEM it waits for its
+// last MMA with the full limit (kTcWaitPolls); if that wait also runs out it
+// counts counters[3]: the columns were released with an MMA possibly still
+// writing them, and the step's results are not to be trusted.  The persistent
 // grid stages the weights once per CTA.
 template <class T, int TY, bool PERSIST>
 __global__ void __launch_bounds__(kTileX, tc_rows(TY) == 1 ? 5 : 3)
     stream_collide_surr_tc(const T* __restrict__ fin, T* __restrict__ fout, const ProbDev* __restrict__ probs,
                            int nprob, int ntiles, int64_t plane, InvLimitsF L,
-                           unsigned long long* __restrict__ counters, const uint4* __restrict__ wtc) {
+                           unsigned long long* __restrict__ counters, const uint4* __restrict__ wtc, int polls) {
   constexpr int R = tc_rows(TY);
   constexpr int RPT = (TY + R - 1) / R;  // rounds per tile
   constexpr int kCols = R * kH;          // TMEM columns
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(kTileX, tc_rows(TY) == 1 ? 5 : 3)
   // releases the CTA and tells every thread whether the wait succeeded
   auto wait_round = [&]() -> bool {
     bool done = true;
-    if (tid == 0) done = tc::mbar_wait(&mbar, phase, kTcSpin);
+    if (tid == 0) done = tc::mbar_wait(&mbar, phase, polls);
     phase ^= 1u;
     const bool any_bad = __syncthreads_or(!done) != 0;
     tc::fence_after();
@@ -488,7 +489,8 @@ __global__ void __launch_bounds__(kTileX, tc_rows(TY) == 1 ? 5 : 3)
   cp_async_wait_all();
   if (failed && tid == 0) {  // failed is uniform across the CTA
     atomicAdd(&counters[2], 1ull);
-    tc::mbar_wait(&mbar, last, kTcSpin);  // the last round, if it is still in flight
+    // the last round, if it is still in flight, with the full limit
+    if (!tc::mbar_wait(&mbar, last, kTcWaitPolls)) atomicAdd(&counters[3], 1ull);
   }
   flush_counts(nfb, nev, counters);
   tc::fence_before();

@@ -44,10 +44,10 @@ static void go_surr_tc(unsigned grid, cudaStream_t s, const StepArgs& a, unsigne
   const uint4* w = (const uint4*)wtc;
   if ((int)grid < a.ntiles)
     stream_collide_surr_tc<T, TY, true><<<grid, kTileX, smem, s>>>((const T*)a.in, (T*)a.out, a.probs, a.nprob,
-                                                                   a.ntiles, a.plane, a.limf, c, w);
+                                                                   a.ntiles, a.plane, a.limf, c, w, a.tc_polls);
   else
     stream_collide_surr_tc<T, TY, false><<<grid, kTileX, smem, s>>>((const T*)a.in, (T*)a.out, a.probs, a.nprob,
-                                                                    a.ntiles, a.plane, a.limf, c, w);
+                                                                    a.ntiles, a.plane, a.limf, c, w, a.tc_polls);
 }
 
 // Sets one instantiation's shared-memory attributes and returns the CTAs

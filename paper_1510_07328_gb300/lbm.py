@@ -86,7 +86,7 @@ def _load():
         "lbm_destroy": (C.c_int, [V]),
         "lbm_last_error": (C.c_char_p, [V]),
         "lbm_launch_count": (C.c_int64, [V]),
-        "lbm_conservation_sums_static": (C.c_int, [V, C.c_int32, C.c_int32, C.c_int32, V, V]),
+        "lbm_conservation_sums_static": (C.c_int, [V, C.c_int32, C.c_int32, V, C.c_int32, V, V]),
         "lbm_set_tiling": (C.c_int, [V, C.c_int32, C.c_int32]),
         "lbm_get_tiling": (C.c_int, [V, C.POINTER(lbm_tiling)]),
         "lbm_autotune": (C.c_int, [V, C.c_int32, C.POINTER(lbm_tiling)]),
@@ -98,6 +98,7 @@ def _load():
         "lbm_surrogate_load": (C.c_int, [V, V]),
         "lbm_surrogate_stats": (C.c_int, [V, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "lbm_surrogate_engine": (C.c_int, [V, C.c_int32]),
+        "lbm_surrogate_wait_limit": (C.c_int, [V, C.c_int32]),
         "lbm_set_obstacles": (C.c_int, [V, C.c_int32, V, C.c_int32]),
         "lbm_set_force": (C.c_int, [V, C.c_int32, C.c_double, C.c_double]),
     }
@@ -113,7 +114,8 @@ EXPORTS = ("lbm_create", "lbm_init_riemann", "lbm_step", "lbm_moments", "lbm_get
            "lbm_set_populations", "lbm_destroy", "lbm_last_error", "lbm_launch_count",
            "lbm_conservation_sums_static", "lbm_set_tiling", "lbm_get_tiling", "lbm_autotune",
            "lbm_surrogate_targets", "lbm_surrogate_loss_grad", "lbm_surrogate_train", "lbm_surrogate_eval",
-           "lbm_surrogate_load", "lbm_surrogate_stats", "lbm_surrogate_engine", "lbm_set_obstacles",
+           "lbm_surrogate_load", "lbm_surrogate_stats", "lbm_surrogate_engine", "lbm_surrogate_wait_limit",
+           "lbm_set_obstacles",
            "lbm_set_force")
 LBM_SURROGATE_FP32_PIPE, LBM_SURROGATE_TENSOR_CORES, LBM_SURROGATE_WARP_MMA = 0, 1, 2
 NPARAM = 4482
@@ -347,18 +349,39 @@ def lbm_surrogate_engine(ctx, engine: str = "tensor"):
     _check(LIB.lbm_surrogate_engine(ctx, SURROGATE_ENGINES[engine]), ctx)
 
 
-def lbm_surrogate_stats(ctx) -> dict:
+def lbm_surrogate_wait_limit(ctx, polls: int):
+    """Poll limit of the tensor-core engine's waits between layers (polls < 0:
+    the default; 0: every such wait gives up at once)."""
+    _check(LIB.lbm_surrogate_wait_limit(ctx, int(polls)), ctx)
+
+
+def lbm_surrogate_stats(ctx, allow_timeout: bool = False) -> dict:
+    """Counts since the context was created.  A timed-out tensor-core wait
+    raises LbmError(LBM_ETIMEOUT) unless allow_timeout, in which case the
+    counts come back with "status" and "message" set."""
     fb = C.c_int64()
     ev = C.c_int64()
-    _check(LIB.lbm_surrogate_stats(ctx, C.byref(fb), C.byref(ev)), ctx)
-    return {"fallbacks": fb.value, "evaluations": ev.value}
+    st = LIB.lbm_surrogate_stats(ctx, C.byref(fb), C.byref(ev))
+    if st != LBM_OK and not (allow_timeout and st == LBM_ETIMEOUT):
+        _check(st, ctx)
+    out = {"fallbacks": fb.value, "evaluations": ev.value, "status": st}
+    if st != LBM_OK:
+        out["message"] = LIB.lbm_last_error(ctx).decode()
+    return out
 
 
-def lbm_conservation_sums_static(f, nx: int, ny: int, out, stat="fd", stream=None):
+def lbm_conservation_sums_static(f, nx: int, ny: int, out, stat="fd", solid=None, stream=None):
     """Conservation totals of device FP64 populations f[9][ny][nx] into the
-    device array out (6 doubles), without any device allocation: for callers
-    that may not call cudaMalloc.  Returns the status code (0 = LBM_OK)."""
-    return int(LIB.lbm_conservation_sums_static(C.c_void_p(_ptr(f)), int(nx), int(ny), STAT[stat],
+    device array out (6 doubles), without any allocation: for callers that
+    may not call cudaMalloc.  solid: optional device mask (one byte per cell,
+    nonzero = obstacle), left out of the totals.  Returns the status code
+    (0 = LBM_OK; the message of a failure is lbm_last_error(None))."""
+    sp = None
+    if solid is not None:
+        if not solid.is_contiguous() or solid.element_size() != 1:
+            raise ValueError("the solid mask must be a contiguous 1-byte device tensor")
+        sp = solid.data_ptr()
+    return int(LIB.lbm_conservation_sums_static(C.c_void_p(_ptr(f)), int(nx), int(ny), C.c_void_p(sp), STAT[stat],
                                                 C.c_void_p(_ptr(out)), C.c_void_p(stream or 0)))
 
 
