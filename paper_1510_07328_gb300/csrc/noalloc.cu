@@ -15,15 +15,22 @@
 // cudaGetSymbolAddress, with that device current, and passed to the kernels.
 // That look-up, and a one-thread kernel that fills the inversion limits, run
 // on the first call on each device, so that first call should come before any
-// stream capture.
+// stream capture.  The looked-up addresses are cached per device index for
+// the life of the process: after cudaDeviceReset they are stale, so a process
+// that resets a device must not call this entry point on it again.
 //
 // Every call shares the array.  Each call writes every partial it later reads,
 // so nothing needs clearing between calls, but calls whose kernels overlap on
 // the GPU (different streams, or different host threads) race on the array:
 // serialise them.
+//
+// The cell limit (kStaticMaxCells) is a policy, not a capacity: the kernel is
+// a grid-stride loop over at most kStaticMaxBlocks blocks, so the scratch
+// array would serve any size; the limit bounds the work of one call.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstdio>
 #include <mutex>
 
 #include "fd_device.cuh"
@@ -51,14 +58,20 @@ InvLimits* g_limits_ptr[kMaxDevices] = {};
 
 // Per-cell sums of n, j, E, clamped inversions and non-finite states over the
 // FP64 population array f[9][cells]; fixed-order block reduction into the
-// partials (same order as the regular diagnostics).
+// partials (same order as the regular diagnostics).  Cells marked in solid
+// (one byte per cell, same order as f; NULL: none) are obstacles and are left
+// out, as lbm_moments leaves them out.  A cell counts as clamped when its
+// finite J_2 lies outside the inversion's interval, the rule of lbm_moments
+// (no inversion is needed for the count).
 template <int STAT>
 __global__ void __launch_bounds__(kStaticThreads) static_sums_kernel(const double* __restrict__ f, int64_t cells,
+                                                                     const uint8_t* __restrict__ solid,
                                                                      const InvLimits* __restrict__ lim,
                                                                      double* __restrict__ partials) {
   double acc[kNPartial] = {0, 0, 0, 0, 0, 0};
   const InvLimits L = *lim;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cells; i += (int64_t)gridDim.x * blockDim.x) {
+    if (solid != nullptr && solid[i] != 0) continue;
     double v[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) v[a] = f[a * cells + i];
@@ -69,7 +82,8 @@ __global__ void __launch_bounds__(kStaticThreads) static_sums_kernel(const doubl
     int cl = 0;
     if (STAT == LBM_STAT_FD) {
       const double ux = jx / n, uy = jy / n;
-      invert_j2(1.5 * (E / n - (ux * ux + uy * uy)), L, &cl);
+      const double J2 = 1.5 * (E / n - (ux * ux + uy * uy));
+      cl = (isfinite(J2) && (J2 >= L.j2_hi || J2 <= L.j2_lo)) ? 1 : 0;
     }
     bool fin = isfinite(n) && isfinite(jx) && isfinite(jy) && isfinite(E);
 #pragma unroll
@@ -155,28 +169,51 @@ lbm_status ensure_setup(int dev, cudaStream_t stream, double** partials, InvLimi
 
 }  // namespace
 
-extern "C" lbm_status lbm_conservation_sums_static(const double* f, int32_t nx, int32_t ny, int32_t stat, double* out,
-                                                   void* cuda_stream) {
-  if (!f || !out) return LBM_EINVAL;
-  if (nx < 1 || ny < 1) return LBM_EINVAL;
+namespace lbm {
+void set_global_error(const char* m);
+}
+
+// Formats the failure into a stack buffer and stores it for
+// lbm_last_error(NULL) (no allocation), then returns the status.
+static lbm_status static_fail(lbm_status st, const char* what, long long v = -1) {
+  char m[256];
+  if (v >= 0)
+    std::snprintf(m, sizeof(m), "lbm_conservation_sums_static: nx * ny = %lld cells exceeds the limit of %lld "
+                  "(LBM_STATIC_SUMS_MAX_CELLS)", v, (long long)kStaticMaxCells);
+  else
+    std::snprintf(m, sizeof(m), "lbm_conservation_sums_static: %s", what);
+  lbm::set_global_error(m);
+  return st;
+}
+
+extern "C" lbm_status lbm_conservation_sums_static(const double* f, int32_t nx, int32_t ny, const uint8_t* solid,
+                                                   int32_t stat, double* out, void* cuda_stream) {
+  if (!f || !out) return static_fail(LBM_EINVAL, "NULL populations or output");
+  if (nx < 1 || ny < 1) return static_fail(LBM_EINVAL, "nx and ny must be >= 1");
   const int64_t cells = (int64_t)nx * ny;
-  if (cells > kStaticMaxCells) return LBM_EINVAL;  // beyond what the static partials cover
-  if (stat < LBM_STAT_FD || stat > LBM_STAT_MB) return LBM_EINVAL;
+  if (cells > kStaticMaxCells) return static_fail(LBM_EINVAL, "", (long long)cells);
+  if (stat < LBM_STAT_FD || stat > LBM_STAT_MB) return static_fail(LBM_EINVAL, "bad stat");
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ECUDA;
-  if (dev < 0 || dev >= kMaxDevices) return LBM_EUNSUPPORTED;
+  if (cudaGetDevice(&dev) != cudaSuccess) return static_fail(LBM_ECUDA, "cudaGetDevice failed");
+  if (dev < 0 || dev >= kMaxDevices) return static_fail(LBM_EUNSUPPORTED, "device index above 63");
   cudaStream_t s = (cudaStream_t)cuda_stream;
   double* partials = nullptr;
   InvLimits* limits = nullptr;
   const lbm_status st = ensure_setup(dev, s, &partials, &limits);
-  if (st != LBM_OK) return st;
+  if (st != LBM_OK) return static_fail(st, "set-up on this device failed");
   const int64_t want = (cells + kStaticThreads - 1) / kStaticThreads;
   const int blocks = (int)(want < kStaticMaxBlocks ? want : kStaticMaxBlocks);
   switch (stat) {
-    case LBM_STAT_FD: static_sums_kernel<LBM_STAT_FD><<<blocks, kStaticThreads, 0, s>>>(f, cells, limits, partials); break;
-    case LBM_STAT_FD_T0: static_sums_kernel<LBM_STAT_FD_T0><<<blocks, kStaticThreads, 0, s>>>(f, cells, limits, partials); break;
-    default: static_sums_kernel<LBM_STAT_MB><<<blocks, kStaticThreads, 0, s>>>(f, cells, limits, partials); break;
+    case LBM_STAT_FD:
+      static_sums_kernel<LBM_STAT_FD><<<blocks, kStaticThreads, 0, s>>>(f, cells, solid, limits, partials);
+      break;
+    case LBM_STAT_FD_T0:
+      static_sums_kernel<LBM_STAT_FD_T0><<<blocks, kStaticThreads, 0, s>>>(f, cells, solid, limits, partials);
+      break;
+    default: static_sums_kernel<LBM_STAT_MB><<<blocks, kStaticThreads, 0, s>>>(f, cells, solid, limits, partials); break;
   }
   static_final_kernel<<<1, 256, 0, s>>>(partials, blocks, out);
-  return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return static_fail(LBM_ECUDA, cudaGetErrorString(e));
+  return LBM_OK;
 }

@@ -54,10 +54,46 @@ def test_static_sums_match_lbm_moments_twice(L):
     lat.close()
 
 
+def test_static_sums_leave_obstacle_cells_out(L):
+    """With the obstacle mask of an lbm_set_obstacles context, the totals
+    equal lbm_moments' diagnostics (solid cells keep their initial
+    populations and are left out of both), on two calls in a row; without the
+    mask the solid cells' mass is counted, so the mask is what makes them
+    agree."""
+    import torch
+
+    p = inputs.random_field(48, 20, 5, tau=0.8, t_lo=0.3, t_hi=0.6, u_max=0.05)
+    solid = inputs.disc_mask(48, 20, [(12, 6), (33, 14)], 3)
+    lat = L.Lattice([p], stat="mb", prec="f64")
+    lat.set_obstacles(solid)
+    lat.set_force(2e-5, -1e-5)
+    lat.init()
+    f = torch.empty((9, p.ny, p.nx), dtype=torch.float64, device="cuda")
+    out = torch.full((6,), float("nan"), dtype=torch.float64, device="cuda")
+    mask = torch.from_numpy(solid.astype(np.uint8)).cuda()
+    for call in range(2):
+        lat.step(2 + call)
+        ref = _totals(L.lbm_moments(lat.ctx, 0, diag=True))
+        L.lbm_get_populations(lat.ctx, 0, f, on_device=True)
+        torch.cuda.synchronize()
+        assert L.lbm_conservation_sums_static(f, p.nx, p.ny, out, stat="mb", solid=mask) == L.LBM_OK
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        np.testing.assert_allclose(got[:4], ref[:4], rtol=1e-12, atol=1e-12 * abs(ref[0]))
+        assert got[4] == ref[4] and got[5] == ref[5]
+        out.fill_(float("nan"))
+    assert L.lbm_conservation_sums_static(f, p.nx, p.ny, out, stat="mb") == L.LBM_OK
+    torch.cuda.synchronize()
+    assert out.cpu().numpy()[0] > ref[0] + 0.5 * solid.sum() * p.n.min()
+    lat.close()
+
+
 def test_static_sums_reject_size_above_limit(L):
     import torch
 
     f = torch.zeros((9, 1), dtype=torch.float64, device="cuda")
     out = torch.zeros((6,), dtype=torch.float64, device="cuda")
     assert L.lbm_conservation_sums_static(f, 4097, 4096, out) == L.LBM_EINVAL
+    assert "exceeds the limit" in L.lbm_last_error(None)
     assert L.lbm_conservation_sums_static(f, 0, 4, out) == L.LBM_EINVAL
+    assert "nx and ny" in L.lbm_last_error(None)
