@@ -273,37 +273,120 @@ def profiled_traffic(kernel: str, workload: str, cells: int):
 # ---------------------------------------------------------------- oracle arm
 
 
-def oracle_sample_mlups(L: int, tau: float, seconds: float, window: int = 48):
-    """Time the CPU oracle on a window of the workload (periodic window
-    stand-in), as many steps as fit in ~`seconds`."""
+def _oracle_window_worker(job):
+    """One host core: advance one oracle window for about job["seconds"] of
+    stepping (or exactly job["steps"] timed steps), re-initialised from its
+    initial state every job["window_steps"] steps as the GPU arm is, so that no
+    non-finite state is ever timed.  The W warm-up steps of every window are
+    untimed.  Returns (cell updates timed, seconds timed, steps timed)."""
+    import numpy as _np
+
+    f0 = job["f0"]
+    step = _oracle_step(job)
+    cells = int(_np.prod(f0.shape[1:]))
+    timed = 0.0
+    steps = 0
+    with _np.errstate(invalid="ignore", divide="ignore", over="ignore"):
+        while True:
+            f = f0
+            for _ in range(job["warmup"]):
+                f = step(f)
+            for _ in range(job["window_steps"]):
+                t0 = time.perf_counter()
+                f = step(f)
+                timed += time.perf_counter() - t0
+                steps += 1
+                if (job.get("steps") and steps >= job["steps"]) or (not job.get("steps") and timed >= job["seconds"]):
+                    return cells * steps, timed, steps
+
+
+def _oracle_step(job):
+    """The oracle's step for a job: d2v9 (oracle/lbm.py), d1v3
+    (oracle/lbm1d.py) or d2v9 with obstacles and a force (oracle/porous.py)."""
+    kind = job.get("kind", "d2v9")
+    stat = job.get("stat", "fd")
+    if kind == "d1v3":
+        from oracle import lbm1d
+
+        return lambda f: lbm1d.step(f, job["tau"], stat)
+    if kind == "porous":
+        from oracle import porous
+
+        return lambda f: porous.step(f, job["solid"], job["tau"], stat, tuple(job["force"]))
+    from oracle import lbm as olbm
+
+    p = olbm.Params(tau=job["tau"], stat=stat, bc_x=job.get("bc_x", "periodic"), bc_y=job.get("bc_y", "periodic"))
+    return lambda f: olbm.step(f, p)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_pool_mlups(jobs, processes: int):
+    """Run the oracle jobs in a pool of `processes` spawned workers (spawn:
+    the parent has a CUDA context); MLUPS = all cell updates / the longest
+    worker's timed seconds."""
+    import multiprocessing as mp
+
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    os.environ.setdefault("MKL_NUM_THREADS", "1")
+    with mp.get_context("spawn").Pool(processes) as pool:
+        res = pool.map(_oracle_window_worker, jobs)
+    updates = sum(r[0] for r in res)
+    secs = max(r[1] for r in res)
+    return updates / secs / 1e6, res
+
+
+def smooth_t_windows(L: int, tau: float, count: int, window: int = 48, stat: str = "fd"):
+    """count initial oracle states: window x window pieces of the smooth-t
+    lattice straddling the density step at x = L/2, at different rows
+    (periodic wrap in place of the rest of the lattice)."""
     from oracle import lbm as olbm
     from paper_1510_07328_gb300 import inputs
 
-    t = inputs.smooth_t_field(L, rows=slice(L // 2 - window // 2, L // 2 + window // 2))
     x0 = L // 2 - window // 2
-    t = t[:, x0:x0 + window]
     xs = np.arange(x0, x0 + window)
     n = np.where(xs < L // 2, 1.0, 0.8)[None, :].repeat(window, 0)
     z = np.zeros_like(n)
-    f = olbm.init_equilibrium(n, z, z, t)
-    p = olbm.Params(tau=tau)
-    steps = 0
-    t0 = time.perf_counter()
-    while True:
-        f = olbm.step(f, p)
-        steps += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
-    return window * window * steps / el / 1e6, steps, window, el
+    tfield = inputs.smooth_t_field(L)
+    out = []
+    for k in range(count):
+        y0 = (k * (L // max(count, 1)) + L // 2 - window // 2) % (L - window)
+        t = tfield[y0:y0 + window, x0:x0 + window]
+        out.append(olbm.init_equilibrium(n, z, z, t, stat))
+    return out
 
 
-def oracle_workload(a):
-    """A bounded sample of the workload for the CPU oracle: (step, state, cells,
-    description).  Windows wrap periodically in place of the rest of the
-    lattice."""
+def oracle_sample_mlups(L: int, tau: float, seconds: float, window: int = 48):
+    """The CPU oracle on windows of the smooth-t workload: one core alone, then
+    every host core at once (independent windows, one per core).  Each window
+    restarts from its initial state every 25 steps after 3 warm-up steps, the
+    regime of the GPU arm's timed windows."""
+    cores = host_cores()
+    f0s = smooth_t_windows(L, tau, cores, window)
+    one = [{"f0": f0s[0], "tau": tau, "warmup": 3, "window_steps": 25, "seconds": seconds * 0.4}]
+    v1, r1 = oracle_pool_mlups(one, 1)
+    jobs = [{"f0": f, "tau": tau, "warmup": 3, "window_steps": 25, "seconds": seconds * 0.6} for f in f0s]
+    vall, rall = oracle_pool_mlups(jobs, cores)
+    return {"value": vall, "cores": cores, "value_1core": v1,
+            "sample": f"{window}x{window} windows of the lattice at x = L/2 (periodic wrap), one per core; each "
+                      f"restarts from its initial state every 25 timed steps after 3 warm-up steps; "
+                      f"{sum(r[2] for r in rall)} timed steps over {cores} cores in {max(r[1] for r in rall):.1f} s; "
+                      f"1 core alone: {r1[0][2]} steps in {r1[0][1]:.1f} s"}
+
+
+def oracle_jobs(a, count: int):
+    """count bounded samples of the workload for the CPU oracle, one per host
+    core, and a description.  Windows wrap periodically in place of the rest
+    of the lattice."""
     from paper_1510_07328_gb300 import inputs
 
+    base = {"warmup": a.warmup, "window_steps": 25, "steps": a.steps}
     if a.workload == "d1v3":
         from oracle import lbm1d
 
@@ -311,59 +394,52 @@ def oracle_workload(a):
         xs = np.arange(a.cells1d // 2 - w // 2, a.cells1d // 2 + w // 2)
         n = np.where((xs > a.cells1d / 4) & (xs < 3 * a.cells1d / 4), 1.0, 0.85)
         f = lbm1d.init_equilibrium(n, np.zeros(w), a.stat)
-        return (lambda f: lbm1d.step(f, 0.58, a.stat)), f, w, f"{w} cells of the d1v3 lattice around x = L/2"
+        jobs = [dict(base, f0=f, kind="d1v3", tau=0.58, stat=a.stat) for _ in range(count)]
+        return jobs, f"{w} cells of the d1v3 lattice around x = L/2, one copy per core"
     from oracle import lbm as olbm
 
     if a.workload == "porous":
-        from oracle import porous
-
         w = min(128, a.L)
-        solid = inputs.disc_mask(a.L, a.L, inputs.disc_centres(a.L, a.L, porous_discs(a.L), 3, 13), 3)[:w, :w]
-        z = np.zeros((w, w))
-        f = olbm.init_equilibrium(np.ones((w, w)), z, z, np.full((w, w), 0.5), a.stat)
-        return ((lambda f: porous.step(f, solid, 0.7, a.stat, (1e-6, 0.0))), f, w * w,
-                f"{w}x{w} corner of the porous lattice ({int(solid.sum())} solid cells)")
+        mask = inputs.disc_mask(a.L, a.L, inputs.disc_centres(a.L, a.L, porous_discs(a.L), 3, 13), 3)
+        jobs = []
+        for k in range(count):
+            y0 = (k * w) % (a.L - w)
+            solid = mask[y0:y0 + w, :w]
+            z = np.zeros((w, w))
+            f = olbm.init_equilibrium(np.ones((w, w)), z, z, np.full((w, w), 0.5), a.stat)
+            jobs.append(dict(base, f0=f, kind="porous", solid=solid, tau=0.7, stat=a.stat, force=(1e-6, 0.0)))
+        return jobs, f"{w}x{w} pieces of the porous lattice (disc mask rows k*{w}), one per core"
     if a.workload == "batched":
-        p = inputs.batched()[0]
-        cols = slice(max(p.nx // 2 - 16, 0), p.nx // 2 + 16)
-        f = olbm.init_equilibrium(p.n[:, cols], p.ux[:, cols], p.uy[:, cols], p.t[:, cols], a.stat)
-        par = olbm.Params(tau=p.tau, stat=a.stat)
-        return ((lambda f: olbm.step(f, par)), f, f.shape[1] * f.shape[2],
-                f"{f.shape[2]} columns around the step of batched problem 0 ({p.ny} rows)")
-    window = 32
-    t = inputs.smooth_t_field(a.L, rows=slice(a.L // 2 - window // 2, a.L // 2 + window // 2))
-    x0 = a.L // 2 - window // 2
-    t = t[:, x0:x0 + window]
-    xs = np.arange(x0, x0 + window)
-    n = np.where(xs < a.L // 2, 1.0, 0.8)[None, :].repeat(window, 0)
-    z = np.zeros_like(n)
-    f = olbm.init_equilibrium(n, z, z, t, a.stat)
-    p = olbm.Params(tau=a.tau, stat=a.stat)
-    return (lambda f: olbm.step(f, p)), f, window * window, f"{window}x{window} window of the lattice at x = L/2"
+        probs = inputs.batched()
+        jobs = []
+        for k in range(count):
+            p = probs[k % len(probs)]
+            cols = slice(max(p.nx // 2 - 16, 0), p.nx // 2 + 16)
+            f = olbm.init_equilibrium(p.n[:, cols], p.ux[:, cols], p.uy[:, cols], p.t[:, cols], a.stat)
+            jobs.append(dict(base, f0=f, kind="d2v9", tau=p.tau, stat=a.stat))
+        return jobs, "32 columns around the density step of batched problem k (one problem per core)"
+    f0s = smooth_t_windows(a.L, a.tau, count, 32, a.stat)
+    jobs = [dict(base, f0=f, kind="d2v9", tau=a.tau, stat=a.stat) for f in f0s]
+    return jobs, "32x32 windows of the lattice at x = L/2, at different rows, one per core"
 
 
 def run_reference(a, world, rank):
     if rank != 0:
         return
-    step, f, cells, what = oracle_workload(a)
-    # as in the GPU arm: warm-up steps from the initial state, then the timed
-    # steps (states past a few dozen steps of the low-t workloads may turn
-    # non-finite; the timing stands either way)
-    with np.errstate(invalid="ignore", divide="ignore", over="ignore"):
-        for _ in range(a.warmup):
-            f = step(f)
-        t0 = time.perf_counter()
-        for _ in range(a.steps):
-            f = step(f)
-        el = time.perf_counter() - t0
-    mlups = cells * a.steps / el / 1e6
+    cores = host_cores()
+    jobs, what = oracle_jobs(a, cores)
+    # every core advances its own window: W untimed warm-up steps from the
+    # initial state, then the K timed steps, restarting every 25 steps (the
+    # GPU arm's regime: no non-finite state is timed)
+    mlups, res = oracle_pool_mlups(jobs, cores)
+    el = max(r[1] for r in res)
     cfg = workload_config(a, 1, inputs_for_config(a))
-    sample = f"{what} (periodic wrap), {a.steps} steps"
+    sample = f"{what}: {a.steps} timed steps each after {a.warmup} warm-up steps, restarting every 25 steps"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": 0,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": el / a.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "config": cfg,
-        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -378,6 +454,37 @@ def inputs_for_config(a):
 
 
 # ---------------------------------------------------------------- GPU arm
+
+
+def timed_windows(lat, lbm, torch, stream, dev_fields, a, world, max_seconds: float = 20.0):
+    """Timed windows of K steps, each after a fresh initialisation and W
+    untimed warm-up steps, with a barrier and a synchronise on both sides;
+    CUDA events on the library's stream.  Repeats until about a second of
+    timed work (or a.reps windows).  Returns the window times (ms) and the
+    library's kernel launches in the last window."""
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    times = []
+    launches = 0
+    t_start = time.perf_counter()
+    while True:
+        with torch.cuda.stream(stream):
+            lat.init(fields_on_device=dev_fields)
+            lat.step(a.warmup)
+        l0 = lbm.lbm_launch_count(lat.ctx)
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        lat.step(a.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        times.append(ev0.elapsed_time(ev1))
+        launches = lbm.lbm_launch_count(lat.ctx) - l0
+        done = len(times) >= a.reps if a.reps > 0 else (sum(times) >= 1000.0 or len(times) >= 60
+                                                        or time.perf_counter() - t_start > max_seconds)
+        if done:
+            return times, launches
 
 
 def run_ours(a, world, rank, local):
@@ -452,30 +559,7 @@ def run_ours(a, world, rank, local):
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.15)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    times = []
-    launches = 0
-    reps = a.reps
-    t_start = time.perf_counter()
-    while True:
-        with torch.cuda.stream(stream):
-            lat.init(fields_on_device=dev_fields)
-            lat.step(a.warmup)
-        l0 = lbm.lbm_launch_count(lat.ctx)
-        barrier(world)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        lat.step(a.steps)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        barrier(world)
-        times.append(ev0.elapsed_time(ev1))
-        launches = lbm.lbm_launch_count(lat.ctx) - l0
-        done = len(times) >= reps if reps > 0 else (sum(times) >= 1000.0 or len(times) >= 60
-                                                    or time.perf_counter() - t_start > 20.0)
-        if done:
-            break
+    times, launches = timed_windows(lat, lbm, torch, stream, dev_fields, a, world)
     sampler.stop()
     ms = statistics.median(times)
     ms_max = max_over_ranks(world, ms)
@@ -524,15 +608,118 @@ def run_ours(a, world, rank, local):
         "state_after_timed_steps": {"nonfinite_frac": nonfinite, "clamped_frac": clamped},
     }
     if not a.no_extras and rank == 0 and a.workload == "smooth_t":
-        out.update(extras(a, prob, dev_fields, lbm, torch, stream, value, net))
+        out.update(extras(a, prob, dev_fields, lbm, torch, stream, value, net, local))
     del dev_fields
     if rank == 0:
         print(json.dumps(out))
 
 
-def extras(a, prob, dev_fields, lbm, torch, stream, value, net=None):
-    """FP64 comparison on the same lattice, end-to-end timing through host
-    buffers, and the CPU oracle on a bounded sample."""
+def field_errors_vs_fp64(lbm, torch, stream, prob, dev_fields, lr, checkpoints=(10, 20)):
+    """Errors of n, |u| and T of the context lr against the plain FP64 path on
+    the same lattice, each from its own initialisation and through its own
+    moments, after each checkpoint's number of steps."""
+    lat64 = lbm.Lattice([prob], stat="fd", prec="f64", stream=stream.cuda_stream)
+    with torch.cuda.stream(stream):
+        lr.init(fields_on_device=dev_fields)
+        lat64.init(fields_on_device=dev_fields)
+    fa = {k: torch.empty((prob.ny, prob.nx), dtype=torch.float64, device="cuda") for k in ("n", "ux", "uy", "T")}
+    fb = {k: torch.empty_like(v) for k, v in fa.items()}
+    errs = []
+    done = 0
+    for nerr in checkpoints:
+        with torch.cuda.stream(stream):
+            lr.step(nerr - done)
+            lat64.step(nerr - done)
+            lbm.lbm_moments(lr.ctx, 0, n=fa["n"], ux=fa["ux"], uy=fa["uy"], T=fa["T"], on_device=True)
+            lbm.lbm_moments(lat64.ctx, 0, n=fb["n"], ux=fb["ux"], uy=fb["uy"], T=fb["T"], on_device=True)
+        done = nerr
+        torch.cuda.synchronize()
+        ok = torch.isfinite(fb["n"]) & torch.isfinite(fa["n"]) & torch.isfinite(fb["T"]) & torch.isfinite(fa["T"])
+        err = {"steps": nerr, "finite_frac": float(ok.double().mean()),
+               "finite_frac_fp64": float((torch.isfinite(fb["n"]) & torch.isfinite(fb["T"])).double().mean())}
+        for k in ("n", "T"):
+            d = (fa[k] - fb[k])[ok].abs()
+            err[f"{k}_max_abs"] = float(d.max())
+            err[f"{k}_max_rel"] = float((d / fb[k][ok].abs()).max())
+            err[f"{k}_rms_rel"] = float(torch.sqrt(((d / fb[k][ok].abs()) ** 2).mean()))
+        du = torch.sqrt((fa["ux"] - fb["ux"]) ** 2 + (fa["uy"] - fb["uy"]) ** 2)[ok]
+        err["u_max_abs"] = float(du.max())
+        errs.append(err)
+    lat64.close()
+    del fa, fb
+    return errs
+
+
+def surrogate_extras(a, prob, dev_fields, lbm, torch, stream, value, v64, local):
+    """The learned inversion on the same lattice and in the same timed-window
+    regime as the headline: the network trained by the library's kernels on
+    1e6 (n, t) pairs of the exact forward map, then fused into the FP32
+    step, on the tcgen05 engine and on the warp-level MMA engine."""
+    from paper_1510_07328_gb300 import inputs
+
+    n_tr, t_tr = inputs.surrogate_set(1_000_000, seed=4)
+    n_va, t_va = inputs.surrogate_set(16384, seed=5)
+    t0 = time.perf_counter()
+    net, rep = lbm.lbm_surrogate_train(inputs.surrogate_init(11), n_tr, t_tr, n_va, t_va,
+                                       epochs=a.train_epochs, batch=1024, stream=stream.cuda_stream)
+    train_s = time.perf_counter() - t0
+    cells = prob.cells
+    peak, peak_kind = peaks()
+    bytes_per_cell = 18 * BYTES_PER_ELEM[a.prec]
+    tname = {"f32": "float", "bf16": "bf16"}[a.prec]
+    res = {}
+    for engine in ("tensor", "mma"):
+        lat = lbm.Lattice([prob], stat="fd", prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05,
+                          inv="surrogate", surrogate=net, engine=engine)
+        with torch.cuda.stream(stream):
+            lat.init(fields_on_device=dev_fields)
+            lat.step(a.warmup)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.15)
+        times, launches = timed_windows(lat, lbm, torch, stream, dev_fields, a, 1, max_seconds=10.0)
+        sampler.stop()
+        st = lbm.lbm_surrogate_stats(lat.ctx, allow_timeout=True)
+        ms = statistics.median(times)
+        v = cells * a.steps / (ms / 1e3) / 1e6
+        achieved = bytes_per_cell * cells / (ms / 1e3 / a.steps) / 1e9
+        kname = {"tensor": "stream_collide_surr_tc<%s>", "mma": "stream_collide_surr_mma<%s>"}[engine] % tname
+        errs = field_errors_vs_fp64(lbm, torch, stream, prob, dev_fields, lat)
+        lat.close()
+        res[engine] = {
+            "value": v, "unit": "MLUPS", "ms_per_step": ms / a.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "traffic": profiled_traffic(kname, "smooth_t", cells),
+                         "algorithmic_bytes_per_cell": bytes_per_cell, "kernel": kname},
+            "fallback_frac": st["fallbacks"] / max(st["evaluations"], 1),
+            "network_cells_frac": st["evaluations"] / (cells * ((len(times) + 1) * a.warmup + len(times) * a.steps)),
+            "stats_status": st["status"],
+            "field_error_vs_fp64": errs,
+            "speedup_vs_fp64": v / v64,
+            "ratio_to_exact": v / value,
+            "gpu_launches": launches,
+            "clocks": sampler.summary(),
+            "timed_windows": {"count": len(times), "median_ms": ms, "min_ms": min(times), "max_ms": max(times)},
+        }
+    best = max(res, key=lambda e: res[e]["value"])
+    out = dict(res[best])
+    out["engine"] = {"tensor": "tcgen05 MMAs over 128-cell tile rows (TMEM accumulators)",
+                     "mma": "warp-level MMAs, activations in registers"}[best]
+    out["other_engine"] = {k: {"value": r["value"], "frac": r["roofline"]["frac"], "fallback_frac": r["fallback_frac"],
+                               "kernel": r["roofline"]["kernel"]} for k, r in res.items() if k != best}
+    out["train"] = {"pairs": 1_000_000, "epochs": a.train_epochs, "batch": 1024, "seconds": train_s,
+                    "val_rmse_lnT": rep["val_rmse_lnT"], "val_rmse_mu": rep["val_rmse_mu"],
+                    "val_max_rel_x": rep["val_max_rel_x"]}
+    out["network"] = "2-64-64-2, SiLU, FP32 weights (FP16 hi/lo operands on the tensor cores), one third-order " \
+                     "polish on J_2(x) = J_2, residual check, exact fallback"
+    return out
+
+
+def extras(a, prob, dev_fields, lbm, torch, stream, value, net=None, local=0):
+    """FP64 comparison on the same lattice, the learned inversion (when the
+    headline is the exact one), end-to-end timing through host buffers, and
+    the CPU oracle on bounded samples over all host cores."""
     res = {}
     cells = prob.cells
     # plain FP64 GPU path, same lattice
@@ -547,6 +734,7 @@ def extras(a, prob, dev_fields, lbm, torch, stream, value, net=None):
     lat64.step(k64)
     e1.record(stream)
     torch.cuda.synchronize()
+    lat64.close()
     v64 = cells * k64 / (e0.elapsed_time(e1) / 1e3) / 1e6
     res["fp64_gpu"] = {"value": v64, "unit": "MLUPS", "steps": k64}
     res["speedup_vs_fp64"] = value / v64
@@ -554,35 +742,10 @@ def extras(a, prob, dev_fields, lbm, torch, stream, value, net=None):
     eng = a.engine if a.inv == "surrogate" else None
     lr = lbm.Lattice([prob], stat="fd", prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05,
                      inv=a.inv, surrogate=net, engine=eng)
-    with torch.cuda.stream(stream):
-        lr.init(fields_on_device=dev_fields)
-        lat64.init(fields_on_device=dev_fields)
-    fa = {k: torch.empty((prob.ny, prob.nx), dtype=torch.float64, device="cuda") for k in ("n", "ux", "uy", "T")}
-    fb = {k: torch.empty_like(v) for k, v in fa.items()}
-    errs = []
-    done = 0
-    for nerr in (10, 20):
-        with torch.cuda.stream(stream):
-            lr.step(nerr - done)
-            lat64.step(nerr - done)
-            lbm.lbm_moments(lr.ctx, 0, n=fa["n"], ux=fa["ux"], uy=fa["uy"], T=fa["T"], on_device=True)
-            lbm.lbm_moments(lat64.ctx, 0, n=fb["n"], ux=fb["ux"], uy=fb["uy"], T=fb["T"], on_device=True)
-        done = nerr
-        torch.cuda.synchronize()
-        ok = torch.isfinite(fb["n"]) & torch.isfinite(fa["n"]) & torch.isfinite(fb["T"]) & torch.isfinite(fa["T"])
-        err = {"steps": nerr, "finite_frac": float(ok.double().mean())}
-        for k in ("n", "T"):
-            d = (fa[k] - fb[k])[ok].abs()
-            err[f"{k}_max_abs"] = float(d.max())
-            err[f"{k}_max_rel"] = float((d / fb[k][ok].abs()).max())
-            err[f"{k}_rms_rel"] = float(torch.sqrt(((d / fb[k][ok].abs()) ** 2).mean()))
-        du = torch.sqrt((fa["ux"] - fb["ux"]) ** 2 + (fa["uy"] - fb["uy"]) ** 2)[ok]
-        err["u_max_abs"] = float(du.max())
-        errs.append(err)
-    res["field_error_vs_fp64"] = errs
+    res["field_error_vs_fp64"] = field_errors_vs_fp64(lbm, torch, stream, prob, dev_fields, lr)
     lr.close()
-    lat64.close()
-    del fa, fb
+    if a.inv == "exact" and a.prec in ("f32", "bf16"):
+        res["surrogate"] = surrogate_extras(a, prob, dev_fields, lbm, torch, stream, value, v64, local)
     # end to end through the public API with host buffers: H2D of the initial
     # fields, K steps, D2H of the moments
     # inputs and outputs in pinned host memory (filled before the timed region)
@@ -618,10 +781,10 @@ def extras(a, prob, dev_fields, lbm, torch, stream, value, net=None):
                   "cycles_ms": [round(e * 1e3, 2) for e in els],
                   "note": "median of 5 timed cycles (init from pinned host fields + steps + moments to pinned "
                           "host arrays, wall clock) after one untimed cycle"}
-    # CPU oracle on a bounded sample
-    mlups, steps, window, el = oracle_sample_mlups(a.L, a.tau, a.cpu_seconds)
-    res["cpu_baseline"] = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                           "sample": f"{window}x{window} window at x = L/2, {steps} steps in {el:.1f} s"}
+    # CPU oracle on bounded samples: one core, then all host cores
+    cb = oracle_sample_mlups(a.L, a.tau, a.cpu_seconds)
+    res["cpu_baseline"] = {"value": cb["value"], "unit": "MLUPS", "cores": cb["cores"], "kind": "oracle",
+                           "value_1core": cb["value_1core"], "sample": cb["sample"]}
     return res
 
 

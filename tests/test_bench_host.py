@@ -31,12 +31,25 @@ def test_settle_closure(workload, stat, want):
 def test_oracle_sample_takes_a_finite_step(workload):
     a = args(workload)
     bench.settle_closure(a)
-    step, f, cells, what = bench.oracle_workload(a)
-    assert cells == f[0].size and cells > 0 and what
-    g = step(f)
-    assert g.shape == f.shape and np.isfinite(g).all()
-    # one collision conserves the mass of the sample (periodic wrap)
-    assert abs(g.sum() - f.sum()) < 1e-12 * abs(f.sum())
+    jobs, what = bench.oracle_jobs(a, 2)
+    assert len(jobs) == 2 and what
+    for job in jobs:
+        f = job["f0"]
+        g = bench._oracle_step(job)(f)
+        assert g.shape == f.shape and np.isfinite(g).all()
+        # one collision conserves the mass of the sample (periodic wrap)
+        assert abs(g.sum() - f.sum()) < 1e-12 * abs(f.sum())
+
+
+def test_oracle_worker_restarts_windows_and_counts_timed_steps():
+    """The pool worker times only steps (warm-up and restarts untimed) and
+    restarts every window_steps steps, so 30 steps of a 25-step window run
+    from two fresh starts."""
+    a = args("smooth_t")
+    jobs, _ = bench.oracle_jobs(a, 1)
+    job = dict(jobs[0], steps=30, warmup=1, window_steps=25)
+    updates, secs, steps = bench._oracle_window_worker(job)
+    assert steps == 30 and updates == 30 * job["f0"][0].size and secs > 0
 
 
 @pytest.mark.parametrize("workload", ["smooth_t", "batched", "d1v3", "porous"])
