@@ -313,9 +313,10 @@ lbm_status lbm_surrogate_load(lbm_ctx* ctx, const float* params);
 enum { LBM_SURROGATE_FP32_PIPE = 0, LBM_SURROGATE_TENSOR_CORES = 1, LBM_SURROGATE_WARP_MMA = 2 };
 lbm_status lbm_surrogate_engine(lbm_ctx* ctx, int32_t engine);
 
-/* Cells that went through the network (finite J_2 inside the clamp
- * interval), and those of them that fell back to the exact inversion, since
- * the context was created.  Synchronises.  Returns LBM_ETIMEOUT (counts still
+/* Cells that went through the network (n and delta = 3/2 - J_2 inside the
+ * network's training domain: n in [0.5, 2], t = T/T_F in [0.005, 0.3]; the
+ * other cells take the exact inversion directly), and those of them that fell
+ * back to the exact inversion, since the context was created.  Synchronises.  Returns LBM_ETIMEOUT (counts still
  * filled) if a tensor-core wait ever gave up.  After a wait between layers
  * gave up, the CTA concerned served its remaining cells by the exact
  * inversion: the results stand.  If the wait for the last MMA before tensor

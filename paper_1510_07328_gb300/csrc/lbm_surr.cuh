@@ -62,10 +62,10 @@ __device__ __forceinline__ float j4_polish_f(float x0, float delta, const InvLim
   return j4_from_delta_f(delta, L, &xx);
 }
 
-// Cells the network handles: finite J_2 inside the clamp interval.
-__device__ __forceinline__ bool net_cell(float delta, const InvLimitsF& L) {
-  const float J2 = 1.5f - delta;
-  return J2 == J2 && J2 < L.j2_hi && J2 > L.j2_lo;
+// Cells the network serves: (n, delta) inside its training domain (which
+// lies inside the clamp interval of the inversion); false for NaN.
+__device__ __forceinline__ bool net_cell(float n, float delta) {
+  return n >= kSurNLo && n <= kSurNHi && delta >= kSurDeltaLo && delta <= kSurDeltaHi;
 }
 
 // x_0 = mu/T from the network's outputs (y_0, y_1).
@@ -77,7 +77,7 @@ __device__ __forceinline__ float x_from_outputs(float y0, float y1) {
 // gives (T, mu) from (n, e), e = 2 n J_2/3 entering as delta = 3/2 - J_2).
 __device__ __forceinline__ float j4_surrogate_f(float n, float delta, const InvLimitsF& L, const MlpParams& W,
                                                 int* fallback) {
-  if (!net_cell(delta, L)) {  // non-finite or clamped: the exact path handles it
+  if (!net_cell(n, delta)) {  // outside the network's domain: the exact path handles it
     float xx;
     return j4_from_delta_f(delta, L, &xx);
   }
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kTileX) stream_collide_surr(const T* __restric
         int fb = 0;
         const float J4 = j4_surrogate_f(m.n, m.delta, L, W, &fb);
         nfb += (unsigned)fb;
-        nev += net_cell(m.delta, L) ? 1u : 0u;
+        nev += net_cell(m.n, m.delta) ? 1u : 0u;
         relax_store_dev<T, STAT_FD>(P, g, m, 1.5f - m.delta, J4, fout, plane, off);
       }
     }
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(kTileX, tc_rows(TY) == 1 ? 5 : 3)
         for (int a = 0; a < 9; ++a) g[a] = stage_pop<T>(st, a, bits >> (9 * r));
         m[r] = dev_moments(P, g);
       }
-      use[r] = act[r] && net_cell(m[r].delta, L);
+      use[r] = act[r] && net_cell(m[r].n, m[r].delta);
     }
     const uint32_t bits_nxt = prefetch(nxt, stage ^ 1);
     float yo[R][2];

@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kTileX, 5)
         for (int a = 0; a < 9; ++a) g[a] = gn[a];
         const int off = offn;
         const CellMom m = dev_moments(P, g);
-        const bool use = act && net_cell(m.delta, L);
+        const bool use = act && net_cell(m.n, m.delta);
         float yo0 = 0.0f, yo1 = 0.0f;
         if (__any_sync(wm::kFull, use)) {
           float i0 = 0.0f, i1 = 0.0f;

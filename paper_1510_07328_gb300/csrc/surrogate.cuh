@@ -25,6 +25,15 @@ constexpr float kSurLdMid = -5.3f, kSurLdHalf = 3.7f;
 constexpr float kSurLnTMid = -5.09f, kSurLnTHalf = 0.5f;
 constexpr float kSurMuMid = 0.1985f, kSurMuHalf = 0.12f;
 
+// The network's domain: the ranges of its training set, n in [0.5, 2] and
+// t = T/T_F in [0.005, 0.3], the latter as delta = 3/2 - J_2 in
+// [delta(t = 0.3), delta(t = 0.005)] (D = 2, values of the exact forward map
+// t -> x -> J_2).  Only cells inside it go through the network; the others
+// take the exact inversion (an extrapolating network would fail the residual
+// check there anyway).
+constexpr float kSurNLo = 0.5f, kSurNHi = 2.0f;
+constexpr float kSurDeltaLo = 1.2332948e-4f, kSurDeltaHi = 0.19829931f;
+
 // Offsets into the flat parameter vector.
 constexpr int kOW1 = 0, kOB1 = kOW1 + 2 * kH, kOW2 = kOB1 + kH, kOB2 = kOW2 + kH * kH, kOW3 = kOB2 + kH,
               kOB3 = kOW3 + 2 * kH;

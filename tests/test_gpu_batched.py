@@ -6,6 +6,7 @@ import pytest
 
 from oracle import lbm as olbm
 from paper_1510_07328_gb300 import inputs
+from parity import rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +51,9 @@ def test_tilings_agree_and_each_is_deterministic(L, prec):
     (the compiler may fuse multiply-adds differently per instantiation), which
     the unstable dynamics amplify (some of these small problems leave the
     equilibrium's domain within about 20 steps), so the comparison across
-    tilings is made after 6 steps; FP64 differences stay at round-off."""
+    tilings is made after 6 steps; FP64 differences stay at round-off.  Cells
+    of the smallest problems that leave the expansion's domain are NaN in
+    every tiling alike; the comparisons require the same NaN cells."""
     probs = small_batch()
     tol = {"f64": 1e-13, "f32": 2e-6}[prec]
     ref = run_tiling(L, probs, prec, 1, 0, steps=6)
@@ -58,11 +61,11 @@ def test_tilings_agree_and_each_is_deterministic(L, prec):
         for ctas in (0, 3, 64):
             got = run_tiling(L, probs, prec, rows, ctas, steps=6)
             for a, r in zip(got, ref):
-                assert np.abs(a - r).max() <= tol * np.abs(r).max(), (rows, ctas)
+                assert rel_err(a, r) <= tol, (rows, ctas)
             first = run_tiling(L, probs, prec, rows, ctas, steps=21)  # 16-step graph + 5 launches
             again = run_tiling(L, probs, prec, rows, ctas, steps=21)
             for a, b in zip(first, again):
-                assert np.array_equal(a, b), (rows, ctas)
+                assert np.array_equal(a, b, equal_nan=True), (rows, ctas)
 
 
 def test_autotune_keeps_state_and_picks_valid_tiling(L):
@@ -75,7 +78,7 @@ def test_autotune_keeps_state_and_picks_valid_tiling(L):
     assert t["rows_per_tile"] in (1, 2, 4, 8) and t["ctas"] >= 0 and t["ms_per_step"] > 0
     after = [lat.populations(i) for i in range(len(probs))]
     for a, b in zip(before, after):
-        assert np.array_equal(a, b)
+        assert np.array_equal(a, b, equal_nan=True)
     lat.step(5)
     lat.close()
 

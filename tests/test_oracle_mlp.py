@@ -54,3 +54,27 @@ def test_silu_derivative():
     z = np.linspace(-6, 6, 101)
     h = 1e-6
     np.testing.assert_allclose(mlp.dsilu(z), (mlp.silu(z + h) - mlp.silu(z - h)) / (2 * h), rtol=1e-7, atol=1e-9)
+
+
+def test_network_domain_constants_match_the_forward_map():
+    """The kernels send a cell through the network only inside its training
+    domain, n in [0.5, 2] and t in [0.005, 0.3], tested on delta = 3/2 - J_2.
+    The delta limits written in the CUDA header are the exact forward map's
+    values at the ends of the t range (FP32-rounded), and the n limits are
+    the training range of inputs.surrogate_set."""
+    import os
+    import re
+
+    from oracle import fd
+    from paper_1510_07328_gb300 import inputs
+
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "paper_1510_07328_gb300", "csrc", "surrogate.cuh")).read()
+    val = {k: float(v) for k, v in re.findall(r"(kSur(?:Delta|N)(?:Lo|Hi)) = ([0-9.e+-]+)f", hdr)}
+    for t, key in ((0.005, "kSurDeltaLo"), (0.3, "kSurDeltaHi")):
+        delta = 1.5 - float(fd.j2_of_x(fd.x_of_t(np.array([t])))[0])
+        assert abs(val[key] - delta) <= 1e-7 * delta, (key, val[key], delta)
+    n, t = inputs.surrogate_set(4096, seed=4)
+    assert val["kSurNLo"] <= n.min() and n.max() <= val["kSurNHi"]
+    assert abs(n.min() - val["kSurNLo"]) < 0.01 and abs(n.max() - val["kSurNHi"]) < 0.01
+    assert 0.005 <= t.min() and t.max() <= 0.3

@@ -56,10 +56,11 @@ def test_static_sums_match_lbm_moments_twice(L):
 
 def test_static_sums_leave_obstacle_cells_out(L):
     """With the obstacle mask of an lbm_set_obstacles context, the totals
-    equal lbm_moments' diagnostics (solid cells keep their initial
-    populations and are left out of both), on two calls in a row; without the
-    mask the solid cells' mass is counted, so the mask is what makes them
-    agree."""
+    equal lbm_moments' diagnostics (which leave solid cells out), on two calls
+    in a row.  Solid cells are never updated, so they keep their initial
+    populations in one of the two buffers: there the totals without the mask
+    exceed those with it by exactly the solid cells' mass, so the mask is
+    what makes them agree."""
     import torch
 
     p = inputs.random_field(48, 20, 5, tau=0.8, t_lo=0.3, t_hi=0.6, u_max=0.05)
@@ -82,10 +83,18 @@ def test_static_sums_leave_obstacle_cells_out(L):
         np.testing.assert_allclose(got[:4], ref[:4], rtol=1e-12, atol=1e-12 * abs(ref[0]))
         assert got[4] == ref[4] and got[5] == ref[5]
         out.fill_(float("nan"))
+    lat.step(1)  # 6 steps: the buffer that still holds the solid cells' initial populations
+    L.lbm_get_populations(lat.ctx, 0, f, on_device=True)
+    assert L.lbm_conservation_sums_static(f, p.nx, p.ny, out, stat="mb", solid=mask) == L.LBM_OK
+    torch.cuda.synchronize()
+    masked = out.cpu().numpy().copy()
     assert L.lbm_conservation_sums_static(f, p.nx, p.ny, out, stat="mb") == L.LBM_OK
     torch.cuda.synchronize()
-    assert out.cpu().numpy()[0] > ref[0] + 0.5 * solid.sum() * p.n.min()
+    unmasked = out.cpu().numpy()
+    solid_mass = float(f.cpu().numpy()[:, solid].sum())
     lat.close()
+    assert solid_mass > 0.5 * solid.sum() * p.n.min()
+    assert abs((unmasked[0] - masked[0]) - solid_mass) <= 1e-12 * unmasked[0]
 
 
 def test_static_sums_reject_size_above_limit(L):
