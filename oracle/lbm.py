@@ -28,6 +28,12 @@ Statistics: "fd" (above), "t0" (theta = 0 closure: J_N = 1 + 2/(N+D) constant,
 the paper's zero-temperature runs) and "mb" (Maxwell-Boltzmann: J_N = 1,
 the standard Hermite D2Q9 limit).  In "t0" and "mb" J_2 is a constant and
 energy is not a collision invariant.
+
+"ft" is the fixed-temperature reading of the moment update, which names only
+I_0 and u_0: theta is a constant of the problem (Params.theta), x follows
+from the density alone, n = I_0 = 2 pi theta f_1(x) (the FD form of I_2N with
+N = 0, D = 2), in closed form x = a + ln(1 - e^{-a}), a = n/(2 pi theta), and
+J_2, J_4 are the FD values at that x.  Energy is not a collision invariant.
 """
 from __future__ import annotations
 
@@ -57,7 +63,8 @@ class Params:
     tau: float
     bc_x: str = "periodic"  # or "bounceback"
     bc_y: str = "periodic"  # or "bounceback"
-    stat: str = "fd"        # "fd", "t0", "mb"
+    stat: str = "fd"        # "fd", "t0", "mb", "ft"
+    theta: float | None = None  # the constant theta of the "ft" closure
 
 
 # ---------------------------------------------------------------- streaming
@@ -128,6 +135,13 @@ def invert_j2(j2: np.ndarray) -> np.ndarray:
     return x
 
 
+def x_of_n_theta(n, theta):
+    """x with 2 pi theta f_1(x) = n, f_1(x) = ln(1 + e^x): x = ln(e^a - 1),
+    a = n/(2 pi theta), written as a + ln(1 - e^{-a}) (no overflow)."""
+    a = np.asarray(n, dtype=np.float64) / (2.0 * math.pi * theta)
+    return a + np.log(-np.expm1(-a))
+
+
 # ---------------------------------------------------------------- equilibrium
 
 
@@ -172,7 +186,7 @@ def init_equilibrium(n, ux, uy, t, stat: str = "fd") -> np.ndarray:
     nn = n.reshape(-1)
     u0 = np.stack([np.asarray(ux, dtype=np.float64).reshape(-1),
                    np.asarray(uy, dtype=np.float64).reshape(-1)], axis=-1)
-    if stat == "fd":
+    if stat in ("fd", "ft"):  # an FD equilibrium at the given t either way
         x = _fd.x_of_t(np.asarray(t, dtype=np.float64).reshape(-1))
         j2 = _fd.j2_of_x(x)
         feq = equilibrium_state(nn, u0, j2, "fd", x)
@@ -181,8 +195,9 @@ def init_equilibrium(n, ux, uy, t, stat: str = "fd") -> np.ndarray:
     return feq.T.reshape((Q,) + shape)
 
 
-def collide(fin: np.ndarray, tau: float, stat: str = "fd"):
-    """BGK collision of pulled populations fin[a, ...]; returns (f*, x)."""
+def collide(fin: np.ndarray, tau: float, stat: str = "fd", theta: float | None = None):
+    """BGK collision of pulled populations fin[a, ...]; returns (f*, x).
+    theta: the problem's constant theta for stat "ft"."""
     shape = fin.shape[1:]
     fl = fin.reshape(Q, -1)
     n, j, En = moments(fl)
@@ -191,6 +206,9 @@ def collide(fin: np.ndarray, tau: float, stat: str = "fd"):
         j2 = j2_from_moments(n, j, En)
         x = invert_j2(j2)
         feq = equilibrium_state(n, u0, j2, "fd", x)
+    elif stat == "ft":
+        x = x_of_n_theta(n, theta)
+        feq = equilibrium_state(n, u0, _fd.j2_of_x(x), "fd", x)
     else:
         x = np.full(n.shape, np.nan)
         feq = equilibrium_state(n, u0, None, stat)
@@ -200,7 +218,7 @@ def collide(fin: np.ndarray, tau: float, stat: str = "fd"):
 
 def step(f: np.ndarray, p: Params) -> np.ndarray:
     fin = stream(f, p.bc_x, p.bc_y)
-    out, _ = collide(fin, p.tau, p.stat)
+    out, _ = collide(fin, p.tau, p.stat, p.theta)
     return out
 
 

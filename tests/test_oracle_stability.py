@@ -63,3 +63,98 @@ def test_energy_closure_1d_unstable():
 
 def test_mb_closure_stable():
     assert growth("mb", 0.0, 0.6, K2D) < 1.0 + 1e-7
+
+
+# ---------------------------------------------------------------- fixed theta
+# The moment update after the LBGK equation names only I_0 and u_0.  Read
+# literally, theta is a constant of the problem and x follows from n alone
+# ("ft" closure of oracle/lbm.py).
+
+
+def ft_growth(t, tau, ks):
+    """Growth factor of the fixed-theta closure about n = 1, u = 0 at the
+    given t (theta = t/(2 pi))."""
+    th = t / (2 * math.pi)
+    z = np.zeros((1, 1))
+    f0 = lbm.init_equilibrium(np.ones((1, 1)), z, z, np.full((1, 1), t), "ft")[:, 0, 0]
+    Jc = np.zeros((9, 9))
+    for b in range(9):
+        d = np.zeros(9)
+        d[b] = 1e-6
+        hi, _ = lbm.collide((f0 + d)[:, None], tau, "ft", th)
+        lo, _ = lbm.collide((f0 - d)[:, None], tau, "ft", th)
+        Jc[:, b] = (hi[:, 0] - lo[:, 0]) / 2e-6
+    worst = 0.0
+    for kx, ky in ks:
+        S = np.diag(np.exp(-1j * (kx * E[:, 0] + ky * E[:, 1])))
+        worst = max(worst, np.abs(np.linalg.eigvals(S @ Jc)).max())
+    return worst
+
+
+KGRID = [(kx, ky) for kx in np.linspace(0, math.pi, 25) for ky in np.linspace(0, math.pi, 25) if kx or ky]
+
+
+def test_fixed_theta_x_from_density():
+    """2 pi theta f_1(x) = n with f_1(x) = ln(1 + e^x), and t = 1/f_1(x) =
+    2 pi theta/n, over the degenerate and the classical side."""
+    from oracle import fd
+
+    n = np.array([0.5, 0.8, 1.0, 1.7, 2.0])
+    for t in (1e-3, 0.05, 0.3, 3.0):
+        th = t / (2 * math.pi)
+        x = lbm.x_of_n_theta(n, th)
+        np.testing.assert_allclose(2 * math.pi * th * fd.fd(1, x), n, rtol=1e-13)
+        np.testing.assert_allclose(fd.t_of_x(x), 2 * math.pi * th / n, rtol=1e-12)
+
+
+def test_fixed_theta_collision_conserves_mass_and_momentum_not_energy():
+    p = __import__("paper_1510_07328_gb300.inputs", fromlist=["random_field"]).random_field(30, 4, 3, tau=0.8)
+    f = lbm.init_equilibrium(p.n, p.ux, p.uy, p.t, "ft")
+    f = f * (1 + 0.01 * np.sin(np.arange(f.size)).reshape(f.shape))
+    out, _ = lbm.collide(f, 0.8, "ft", 0.05 / (2 * math.pi))
+    n0, j0, E0 = lbm.moments(f)
+    n1, j1, E1 = lbm.moments(out)
+    np.testing.assert_allclose(n1, n0, rtol=1e-14)
+    np.testing.assert_allclose(j1, j0, atol=1e-14)
+    assert np.abs(E1 - E0).max() > 1e-6  # relaxes toward the fixed-theta energy
+
+
+def test_fixed_theta_uniform_state_is_fixed_point():
+    th = 0.05 / (2 * math.pi)
+    n = np.full((4, 6), 0.9)
+    z = np.zeros_like(n)
+    f = lbm.init_equilibrium(n, z + 0.03, z - 0.02, 2 * math.pi * th / n, "ft")
+    g = lbm.step(f, lbm.Params(tau=0.7, stat="ft", theta=th))
+    np.testing.assert_allclose(g, f, rtol=0, atol=1e-15)
+
+
+def test_fixed_theta_linear_stability():
+    """Every 1D mode is stable; 2D modes are neutral at the quasi-1D
+    Riemann workload's (t = 0.05, tau = 0.8) and grow at lower t or tau:
+    1.27 at (0.02, 0.6) (the four-quadrant workload's low end), 1.07 at
+    (0.01, 0.8) (the smooth-temperature workload's low end)."""
+    k1 = [(k, 0.0) for k in np.linspace(1e-3, math.pi, 60)]
+    for t, tau in ((0.01, 0.55), (0.05, 0.8), (0.2, 1.0)):
+        assert ft_growth(t, tau, k1) < 1 + 1e-7
+    assert ft_growth(0.05, 0.8, KGRID) < 1 + 1e-7
+    assert ft_growth(0.1, 0.8, KGRID) < 1 + 1e-7
+    assert 1.2 < ft_growth(0.02, 0.6, KGRID) < 1.35
+    assert 1.04 < ft_growth(0.01, 0.8, KGRID) < 1.1
+
+
+def test_fixed_theta_riemann_1000_steps_stay_finite():
+    """The 400 x 4 Riemann problem (n = 1.0 | 0.8, tau = 0.8, bounce-back
+    x-walls) at theta = 0.9 x 0.05/(2 pi) for its full 1000 steps: finite,
+    n within the initial states' range, the transverse momentum at
+    round-off."""
+    from paper_1510_07328_gb300 import inputs
+
+    p = inputs.riemann_1d()
+    th = 0.9 * 0.05 / (2 * math.pi)
+    f = lbm.init_equilibrium(p.n, p.ux, p.uy, 2 * math.pi * th / p.n, "ft")
+    f = lbm.run(f, lbm.Params(tau=p.tau, bc_x=p.bc_x, bc_y=p.bc_y, stat="ft", theta=th), 1000)
+    assert np.isfinite(f).all()
+    n = f.sum(axis=0)
+    assert 0.79 < n.min() and n.max() < 1.01
+    jy = (f[2] - f[4] + f[5] + f[6] - f[7] - f[8]).sum()
+    assert abs(jy) < 1e-11
