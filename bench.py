@@ -248,9 +248,17 @@ KERNEL_SOURCES = {
 }
 
 
+def kernel_family(kernel: str) -> str:
+    """The KERNEL_SOURCES key of a kernel name: the learned-inversion engines
+    (stream_collide_surr_tc, _tc2, _mma) share one family."""
+    import re
+
+    return re.sub(r"_(tc\d*|mma)$", "", kernel.split("<")[0])
+
+
 def kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES[kernel.split("<")[0].replace("_tc", "").replace("_mma", "")]:
+    for f in KERNEL_SOURCES[kernel_family(kernel)]:
         h.update(open(os.path.join(ROOT, "paper_1510_07328_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

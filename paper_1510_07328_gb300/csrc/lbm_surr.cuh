@@ -143,101 +143,48 @@ __global__ void __launch_bounds__(kTileX) stream_collide_surr(const T* __restric
 }
 
 
-// Tile rows per tensor-core round.  Two rows per round (two independent MMA
-// chains in flight) need 128 TMEM columns, 74 KB of shared memory and about
-// 170 registers per thread, leaving 3 CTAs per SM; one row per round leaves 5
-// and measured 12 % faster on the 4096^2 lattice.
+// Rows of a tile per tensor-core round (one: an M = 128 operand per round).
 __host__ __device__ constexpr int tc_rows(int /*TY*/) { return 1; }
-// Dynamic shared memory of the kernel, in this order: the network's operands;
-// per round row the input block (128 x 16 FP16) and the hidden activations
-// (128 x 64 FP16); two stages of pulled populations (per row 9 x 128 words).
+// Dynamic shared memory of the kernel, in this order: the network's operands
+// (kTcBytes), the input block (128 x 16 FP16) and the hidden activations
+// (128 x 64 FP16): 35,328 bytes.
 __host__ __device__ constexpr int tc_smem_x(int /*R*/) { return kTcBytes; }
 __host__ __device__ constexpr int tc_smem_a(int R) { return tc_smem_x(R) + R * kTileX * 16 * 2; }
-__host__ __device__ constexpr int tc_smem_g(int R) { return tc_smem_a(R) + R * kTileX * kH * 2; }
-__host__ __device__ constexpr int tc_smem(int R) { return tc_smem_g(R) + 2 * R * 9 * kTileX * 4; }
-static_assert(tc_smem_a(1) % 16 == 0 && tc_smem_g(2) % 16 == 0, "operand blocks must be 16-byte aligned");
+__host__ __device__ constexpr int tc_smem(int R) { return tc_smem_a(R) + R * kTileX * kH * 2; }
+static_assert(tc_smem_x(1) % 1024 == 512 || tc_smem_x(1) % 16 == 0, "operand blocks must be 16-byte aligned");
+static_assert(tc_smem_a(1) % 16 == 0, "operand blocks must be 16-byte aligned");
+// CTAs the kernel is compiled for per SM: six (80 registers, no spills, with
+// the activations read from TMEM in two halves), the most the shared memory
+// allows.
+constexpr int kTcCtasPerSm = 6;
+// Of every 32 activation pairs of a hidden layer, this many take the FMA-pipe
+// SiLU (tc::silu2_poly) and the rest the MUFU one (tc::silu2_packed): both
+// pipes then share the activations' work.
+constexpr int kTcPolyPairs = 8;
 
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// Starts the asynchronous pull of cell (x, y)'s nine populations into the
-// stage words st + a * 512 bytes (a = 0..8; same sources as gather_dev).
-// 16-bit populations travel in the aligned 4-byte word that holds them; the
-// returned bits say which half (bit a set: the upper one).
-template <class T>
-__device__ __forceinline__ uint32_t prefetch_cell(const T* __restrict__ fin, int64_t plane, const ProbDev& P, int x,
-                                                  int y, bool xin, uint32_t st) {
-  const T* src[9];
-  if (xin && y >= 1 && y <= P.ny - 2) {
-    const int off = (int)P.base + y * P.pitch + x;
-    const int pt = P.pitch;
-    src[0] = fin + off;
-    src[1] = fin + (plane + (off - 1));
-    src[2] = fin + (2 * plane + (off - pt));
-    src[3] = fin + (3 * plane + (off + 1));
-    src[4] = fin + (4 * plane + (off + pt));
-    src[5] = fin + (5 * plane + (off - pt - 1));
-    src[6] = fin + (6 * plane + (off - pt + 1));
-    src[7] = fin + (7 * plane + (off + pt + 1));
-    src[8] = fin + (8 * plane + (off + pt - 1));
-  } else {
-    const PullIdx32 q = pull_index32(P, x, y);
-    auto s = [&](int a, int r, int xs, int opp) -> const T* {
-      return (r < 0 || xs < 0) ? fin + (opp * plane + (q.row + x)) : fin + (a * plane + (r + xs));
-    };
-    src[0] = fin + (q.row + x);
-    src[1] = s(1, q.row, q.xm, 3);
-    src[2] = s(2, q.rm, x, 4);
-    src[3] = s(3, q.row, q.xp, 1);
-    src[4] = s(4, q.rp, x, 2);
-    src[5] = s(5, q.rm, q.xm, 7);
-    src[6] = s(6, q.rm, q.xp, 8);
-    src[7] = s(7, q.rp, q.xp, 5);
-    src[8] = s(8, q.rp, q.xm, 6);
-  }
-  uint32_t bits = 0;
-#pragma unroll
-  for (int a = 0; a < 9; ++a) {
-    uintptr_t p = reinterpret_cast<uintptr_t>(src[a]);
-    if (sizeof(T) == 2) {
-      bits |= (uint32_t)((p >> 1) & 1u) << a;
-      p &= ~(uintptr_t)3;
-    }
-    cp_async4(st + (uint32_t)(a * kTileX * 4), reinterpret_cast<const void*>(p));
-  }
-  return bits;
-}
-
-// Population a of this thread's cell from its stage words.
-template <class T>
-__device__ __forceinline__ float stage_pop(const unsigned char* st, int a, uint32_t bits) {
-  const uint32_t w = *reinterpret_cast<const uint32_t*>(st + a * kTileX * 4);
-  if (sizeof(T) == 4) return __uint_as_float(w);
-  const uint32_t h = ((bits >> a) & 1u) ? (w >> 16) : (w & 0xffffu);
-  return __uint_as_float(h << 16);  // bfloat16 -> float
+// SiLU of one packed pair: pair i of 32 goes to the FMA pipe for every
+// (32 / KP)-th i, to MUFU otherwise.
+template <int KP>
+__device__ __forceinline__ uint32_t silu2_mixed(uint32_t h, int i) {
+  if (KP > 0 && (i % (32 / (KP > 0 ? KP : 1))) == (32 / (KP > 0 ? KP : 1)) - 1) return tc::silu2_poly(h);
+  return tc::silu2_packed(h);
 }
 
 // The FD step with the learned inversion, all three layers on the tensor
-// cores.  Each round serves R = tc_rows(TY) tile rows of 128 cells (one cell
-// per thread and row); every row is an M = 128 operand with its own 64 TMEM
-// columns:
-//  0. the populations of the round were pulled into a shared stage by
-//     cp.async during the previous round; the next round's pull starts as
-//     soon as this round's moments are formed (across tile boundaries of the
-//     persistent sweep);
-//  1. each thread writes its cells' input rows (n, l split into FP16 hi/lo
-//     parts, constant columns for the biases) to sX; one thread issues the
-//     layer-1 MMAs (K = 16, N = 64);
-//  2. each warp reads its 32 lanes back, applies SiLU by packed FP16 tanh
-//     and writes h1 to sA; layer 2 is four K = 16 MMAs against W2 plus one
-//     against the bias block (N = 64), per row;
+// cores.  Tiles and gathers as stream_collide_dev: one cell per thread and
+// tile row, the nine populations pulled into registers, the next row's loads
+// in flight while this row's network runs.  Every tile row is an M = 128
+// operand with its 64 TMEM columns:
+//  1. each thread writes its cell's input row (n, l split into FP16 hi/lo
+//     parts, constant columns for the biases) to sX; a barrier that also
+//     tells whether any cell of the row needs the network (rows without one
+//     skip the MMAs); one thread issues the layer-1 MMAs (K = 16, N = 64);
+//  2. each warp reads its 32 lanes back, applies SiLU (kTcPolyPairs of every
+//     32 pairs on the FMA pipe, the rest on MUFU) and writes h1 to sA; layer
+//     2 is four K = 16 MMAs against W2 plus one against the bias block;
 //  3. the same for h2; layer 3 is N = 16 (rows hi and lo of W3, bias block);
 //     y = D[0..1] + D[2..3];
-//  4. the polish, the residual check and the relaxation per cell, with the
-//     populations read again from the stage.
+//  4. the polish, the residual check and the relaxation per cell.
 // The issuing thread alone waits on the mbarrier, at most `polls` polls per
 // round; a barrier with a reduction (bar.red.or) then releases the CTA with
 // the outcome, so the other warps spend no issue slots on polling.  A CTA
@@ -248,62 +195,51 @@ __device__ __forceinline__ float stage_pop(const unsigned char* st, int a, uint3
 // writing them, and the step's results are not to be trusted.  The persistent
 // grid stages the weights once per CTA.
 template <class T, int TY, bool PERSIST>
-__global__ void __launch_bounds__(kTileX, tc_rows(TY) == 1 ? 5 : 3)
+__global__ void __launch_bounds__(kTileX, kTcCtasPerSm)
     stream_collide_surr_tc(const T* __restrict__ fin, T* __restrict__ fout, const ProbDev* __restrict__ probs,
                            int nprob, int ntiles, int64_t plane, InvLimitsF L,
                            unsigned long long* __restrict__ counters, const uint4* __restrict__ wtc, int polls) {
-  constexpr int R = tc_rows(TY);
-  constexpr int RPT = (TY + R - 1) / R;  // rounds per tile
-  constexpr int kCols = R * kH;          // TMEM columns
   extern __shared__ __align__(1024) unsigned char smem_dyn[];
   unsigned char* const sW = smem_dyn;
-  unsigned char* const sX = smem_dyn + tc_smem_x(R);
-  unsigned char* const sA = smem_dyn + tc_smem_a(R);
-  unsigned char* const sG = smem_dyn + tc_smem_g(R);
+  unsigned char* const sX = smem_dyn + tc_smem_x(1);
+  unsigned char* const sA = smem_dyn + tc_smem_a(1);
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   const int tid = (int)threadIdx.x, warp = tid >> 5;
   for (int i = tid; i < kTcBytes / 16; i += kTileX) reinterpret_cast<uint4*>(sW)[i] = wtc[i];
-#pragma unroll
-  for (int r = 0; r < R; ++r)
-    *reinterpret_cast<uint4*>(sX + r * kTileX * 32 + tc::kmajor_off(tid, 8, kTileX)) = make_uint4(0u, 0u, 0u, 0u);
+  *reinterpret_cast<uint4*>(sX + tc::kmajor_off(tid, 8, kTileX)) = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) tc::mbar_init(&mbar, 1);
-  if (warp == 0) tc::tmem_alloc(&tmem_slot, kCols);
+  if (warp == 0) tc::tmem_alloc(&tmem_slot, kH);
   tc::fence_async_smem();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tmem_slot;
   const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's 32 lanes
-  const uint32_t uA = tc::smem_u32(sA), uX = tc::smem_u32(sX), uW = tc::smem_u32(sW), uG = tc::smem_u32(sG);
+  const uint32_t uA = tc::smem_u32(sA), uX = tc::smem_u32(sX), uW = tc::smem_u32(sW);
   // layers 1 and 2 accumulate in FP16 (their outputs become FP16 operands
   // anyway; the polish and the residual check absorb the rounding), layer 3
   // in FP32
   const uint32_t id64 = tc::idesc_f16_f16(kTileX, kH), id16 = tc::idesc_f16_f32(kTileX, 16);
   constexpr uint32_t kLboA = (kTileX / 8) * 128, kLbo64 = (kH / 8) * 128, kLbo16 = (16 / 8) * 128;
-  constexpr uint32_t kBlkX = kTileX * 16 * 2, kBlkA = kTileX * kH * 2, kRowG = 9 * kTileX * 4;
   uint32_t phase = 0, last = 0;
   bool failed = false;
   unsigned nfb = 0, nev = 0;
 
   auto issue = [&](int layer) {
     if (tid == 0) {
+      if (layer == 1) {
+        tc::mma_f16(tmem, tc::smem_desc(uX, kLboA, 128), tc::smem_desc(uW + kTcB1, kLbo64, 128), id64, 0u);
+      } else {
+        const uint32_t bw = layer == 2 ? uW + kTcB2 : uW + kTcB3;
+        const uint32_t bb = layer == 2 ? uW + kTcB2b : uW + kTcB3b;
+        const uint32_t lbo = layer == 2 ? kLbo64 : kLbo16;
+        const uint32_t id = layer == 2 ? id64 : id16;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const uint32_t d = tmem + (uint32_t)(r * kH), xb = uX + r * kBlkX, ab = uA + r * kBlkA;
-        if (layer == 1) {
-          tc::mma_f16(d, tc::smem_desc(xb, kLboA, 128), tc::smem_desc(uW + kTcB1, kLbo64, 128), id64, 0u);
-        } else {
-          const uint32_t bw = layer == 2 ? uW + kTcB2 : uW + kTcB3;
-          const uint32_t bb = layer == 2 ? uW + kTcB2b : uW + kTcB3b;
-          const uint32_t lbo = layer == 2 ? kLbo64 : kLbo16;
-          const uint32_t id = layer == 2 ? id64 : id16;
-#pragma unroll
-          for (int s = 0; s < kH / 16; ++s)
-            tc::mma_f16(d, tc::smem_desc(ab + (uint32_t)s * 2 * kLboA, kLboA, 128),
-                        tc::smem_desc(bw + (uint32_t)s * 2 * lbo, lbo, 128), id, s > 0 ? 1u : 0u);
-          tc::mma_f16(d, tc::smem_desc(xb, kLboA, 128), tc::smem_desc(bb, lbo, 128), id, 1u);
-        }
+        for (int s = 0; s < kH / 16; ++s)
+          tc::mma_f16(tmem, tc::smem_desc(uA + (uint32_t)s * 2 * kLboA, kLboA, 128),
+                      tc::smem_desc(bw + (uint32_t)s * 2 * lbo, lbo, 128), id, s > 0 ? 1u : 0u);
+        tc::mma_f16(tmem, tc::smem_desc(uX, kLboA, 128), tc::smem_desc(bb, lbo, 128), id, 1u);
       }
       tc::commit(&mbar);
     }
@@ -320,173 +256,124 @@ __global__ void __launch_bounds__(kTileX, tc_rows(TY) == 1 ? 5 : 3)
     return !any_bad;
   };
   // publishes the operand rows written by every thread, and the end of their
-  // TMEM reads, to the issuing thread
-  auto publish = [&]() {
+  // TMEM reads, to the issuing thread; returns whether any thread's flag is set
+  auto publish = [&](bool flag) -> bool {
     tc::fence_async_smem();
     tc::fence_before();
-    __syncthreads();
+    const bool any = __syncthreads_or(flag) != 0;
     tc::fence_after();
+    return any;
   };
-  // SiLU of the FP16 TMEM columns of row r (holding z/2) into row tid of sA
-  // block r: the packed load gives the pairs (k, k + 1) the operand stores
-  auto act_store = [&](int r) {
-    uint32_t v[32];
-    tc::tmem_ld64_pack16(tl + (uint32_t)(r * kH), v);
+  // SiLU of the FP16 TMEM columns (holding z/2) into row tid of sA: the
+  // packed load gives the pairs (k, k + 1) the operand stores
+  auto act_store = [&]() {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      uint4 w;
-      w.x = tc::silu2_packed(v[4 * c + 0]);
-      w.y = tc::silu2_packed(v[4 * c + 1]);
-      w.z = tc::silu2_packed(v[4 * c + 2]);
-      w.w = tc::silu2_packed(v[4 * c + 3]);
-      *reinterpret_cast<uint4*>(sA + r * kBlkA + tc::kmajor_off(tid, 8 * c, kTileX)) = w;
-    }
-  };
-  // round k of this CTA: its problem, tile origin and rows
-  struct Round {
-    int p, x0, yb, y1;
-    bool xin, valid;
-  };
-  auto decode = [&](int k) -> Round {
-    Round rd{0, 0, 0, 0, false, false};
-    const int tile = (int)blockIdx.x + (k / RPT) * (int)gridDim.x;
-    rd.valid = PERSIST ? tile < ntiles : k < RPT;
-    if (rd.valid) {
-      rd.p = nprob == 1 ? 0 : find_problem(probs, nprob, tile);
-      const ProbDev& P = probs[rd.p];
-      const int lt = tile - (int)P.tile_begin;
-      const int ty = lt / P.tiles_x;
-      rd.x0 = (lt - ty * P.tiles_x) * kTileX;
-      rd.yb = ty * TY + (k % RPT) * R;
-      rd.y1 = min(ty * TY + TY, P.ny);
-      rd.xin = rd.x0 >= 1 && rd.x0 + kTileX <= P.nx - 1;
-    }
-    return rd;
-  };
-  auto prefetch = [&](const Round& rd, int stage) -> uint32_t {
-    uint32_t bits = 0;
-    if (rd.valid) {
-      const ProbDev& P = probs[rd.p];
-      const int x = rd.x0 + tid;
+    for (int half = 0; half < 2; ++half) {  // 32 columns at a time: 16 registers live
+      uint32_t v[16];
+      tc::tmem_ld32_pack16(tl + (uint32_t)(32 * half), v);
 #pragma unroll
-      for (int r = 0; r < R; ++r)
-        if (x < P.nx && rd.yb + r < rd.y1)
-          bits |= prefetch_cell<T>(fin, plane, P, x, rd.yb + r, rd.xin,
-                                   uG + (uint32_t)((stage * R + r) * kRowG + tid * 4))
-                  << (9 * r);
+      for (int c = 0; c < 4; ++c) {
+        const int i = 16 * half + 4 * c;  // pair index of v[4 c] within the row's 32 pairs
+        uint4 w;
+        w.x = silu2_mixed<kTcPolyPairs>(v[4 * c + 0], i + 0);
+        w.y = silu2_mixed<kTcPolyPairs>(v[4 * c + 1], i + 1);
+        w.z = silu2_mixed<kTcPolyPairs>(v[4 * c + 2], i + 2);
+        w.w = silu2_mixed<kTcPolyPairs>(v[4 * c + 3], i + 3);
+        *reinterpret_cast<uint4*>(sA + tc::kmajor_off(tid, 8 * (4 * half + c), kTileX)) = w;
+      }
     }
-    cp_async_commit();
-    return bits;
   };
 
-  Round cur = decode(0);
-  uint32_t bits = prefetch(cur, 0);
+  int tile = (int)blockIdx.x;
 #pragma unroll 1
-  for (int k = 0; cur.valid; ++k) {
-    const int stage = k & 1;
-    cp_async_wait_all();
-    const Round nxt = decode(k + 1);
-    const ProbDev& P = probs[cur.p];
-    const int x = cur.x0 + tid;
-    CellMom m[R];
-    bool act[R], use[R];
+  do {
+    const int p = nprob == 1 ? 0 : find_problem(probs, nprob, tile);
+    const ProbDev& P = probs[p];
+    const int lt = tile - (int)P.tile_begin;
+    const int ty = lt / P.tiles_x;
+    const int x0 = (lt - ty * P.tiles_x) * kTileX;
+    const int x = x0 + tid;
+    const bool act = x < P.nx;  // every thread takes part in the barriers
+    const int y0 = ty * TY;
+    const int y1 = min(y0 + TY, P.ny);
+    const bool xin = x0 >= 1 && x0 + kTileX <= P.nx - 1;
+    float gn[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int offn = 0;
+    if (act) offn = gather_dev(fin, plane, P, x, y0, xin, gn);
+#pragma unroll 1
+    for (int y = y0; y < y1; ++y) {
+      float g[9];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      act[r] = x < P.nx && cur.yb + r < cur.y1;
-      m[r] = CellMom{};
-      m[r].n = 1.0f;
-      m[r].delta = 0.1f;
-      if (act[r]) {
-        const unsigned char* st = sG + (stage * R + r) * kRowG + tid * 4;
-        float g[9];
-#pragma unroll
-        for (int a = 0; a < 9; ++a) g[a] = stage_pop<T>(st, a, bits >> (9 * r));
-        m[r] = dev_moments(P, g);
-      }
-      use[r] = act[r] && net_cell(m[r].n, m[r].delta);
-    }
-    const uint32_t bits_nxt = prefetch(nxt, stage ^ 1);
-    float yo[R][2];
-    bool have = false;
-    if (!failed) {
-      bool warp_net = false;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
+      for (int a = 0; a < 9; ++a) g[a] = gn[a];
+      const int off = offn;
+      CellMom m{};
+      m.n = 1.0f;
+      m.delta = 0.1f;
+      if (act) m = dev_moments(P, g);
+      const bool use = act && net_cell(m.n, m.delta);
+      // the next row's loads, in flight during this row's network
+      if (act && y + 1 < y1) offn = gather_dev(fin, plane, P, x, y + 1, xin, gn);
+      float yo0 = 0.0f, yo1 = 0.0f;
+      bool have = false;
+      if (!failed) {
         float i0 = 0.0f, i1 = 0.0f;
-        if (use[r]) {
-          i0 = fminf(fmaxf((m[r].n - kSurNMid) * (1.0f / kSurNHalf), -8.0f), 8.0f);
-          i1 = fminf(fmaxf((__logf(m[r].delta) - kSurLdMid) * (1.0f / kSurLdHalf), -8.0f), 8.0f);
+        if (use) {
+          i0 = (m.n - kSurNMid) * (1.0f / kSurNHalf);
+          i1 = (__logf(m.delta) - kSurLdMid) * (1.0f / kSurLdHalf);
         }
         const __half nh = __float2half_rn(i0), lh = __float2half_rn(i1);
         const __half nl = __float2half_rn(i0 - __half2float(nh)), ll = __float2half_rn(i1 - __half2float(lh));
-        const __half one = __float2half_rn(1.0f);
         uint4 row;
-        __half2 t;
-        t = __halves2half2(nh, nl);
-        row.x = *reinterpret_cast<const uint32_t*>(&t);
-        t = __halves2half2(nh, lh);
-        row.y = *reinterpret_cast<const uint32_t*>(&t);
-        t = __halves2half2(ll, lh);
-        row.z = *reinterpret_cast<const uint32_t*>(&t);
-        t = __halves2half2(one, one);
-        row.w = *reinterpret_cast<const uint32_t*>(&t);
-        *reinterpret_cast<uint4*>(sX + r * kBlkX + tc::kmajor_off(tid, 0, kTileX)) = row;
-        warp_net = warp_net || use[r];
-      }
-      warp_net = __any_sync(0xffffffffu, warp_net);
-      publish();
-#pragma unroll 1
-      for (int layer = 1; layer <= 2 && !failed; ++layer) {
-        issue(layer);
-        failed = !wait_round();
-        if (!failed) {
-          if (warp_net) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) act_store(r);
+        __half2 t2;
+        t2 = __halves2half2(nh, nl);
+        row.x = *reinterpret_cast<const uint32_t*>(&t2);
+        t2 = __halves2half2(nh, lh);
+        row.y = *reinterpret_cast<const uint32_t*>(&t2);
+        t2 = __halves2half2(ll, lh);
+        row.z = *reinterpret_cast<const uint32_t*>(&t2);
+        row.w = 0x3C003C00u;  // (1, 1): the bias columns
+        *reinterpret_cast<uint4*>(sX + tc::kmajor_off(tid, 0, kTileX)) = row;
+        const bool warp_net = __any_sync(0xffffffffu, use);
+        if (publish(use)) {  // uniform: some cell of the row needs the network
+          issue(1);
+          failed = !wait_round();
+          if (!failed) {
+            if (warp_net) act_store();
+            publish(false);
+            issue(2);
+            failed = !wait_round();
           }
-          publish();
-        }
-      }
-      if (!failed) {
-        issue(3);
-        failed = !wait_round();
-        if (!failed && warp_net) {
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
+          if (!failed) {
+            if (warp_net) act_store();
+            publish(false);
+            issue(3);
+            failed = !wait_round();
+          }
+          if (!failed && warp_net) {  // warp-uniform: the TMEM load is .sync.aligned
             float v[4];
-            tc::tmem_ld4(tl + (uint32_t)(r * kH), v);
-            yo[r][0] = v[0] + v[2];
-            yo[r][1] = v[1] + v[3];
+            tc::tmem_ld4(tl, v);
+            yo0 = v[0] + v[2];
+            yo1 = v[1] + v[3];
+            have = true;
           }
-          have = true;
         }
       }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      if (!act[r]) continue;
-      int fb = 0;
-      float J4;
-      if (use[r] && have) {
-        J4 = j4_polish_f(x_from_outputs(yo[r][0], yo[r][1]), m[r].delta, L, &fb);
-      } else {
-        float xx;
-        J4 = j4_from_delta_f(m[r].delta, L, &xx);
-        fb = use[r] ? 1 : 0;
+      if (act) {
+        int fb = 0;
+        float J4;
+        if (use && have) {
+          J4 = j4_polish_f(x_from_outputs(yo0, yo1), m.delta, L, &fb);
+        } else {
+          float xx;
+          J4 = j4_from_delta_f(m.delta, L, &xx);
+          fb = use ? 1 : 0;
+        }
+        nfb += (unsigned)fb;
+        nev += use ? 1u : 0u;
+        relax_store_dev<T, STAT_FD>(P, g, m, 1.5f - m.delta, J4, fout, plane, off);
       }
-      nfb += (unsigned)fb;
-      nev += use[r] ? 1u : 0u;
-      const unsigned char* st = sG + (stage * R + r) * kRowG + tid * 4;
-      float g[9];
-#pragma unroll
-      for (int a = 0; a < 9; ++a) g[a] = stage_pop<T>(st, a, bits >> (9 * r));
-      const int off = (int)P.base + (cur.yb + r) * P.pitch + x;
-      relax_store_dev<T, STAT_FD>(P, g, m[r], 1.5f - m[r].delta, J4, fout, plane, off);
     }
-    cur = nxt;
-    bits = bits_nxt;
-  }
-  cp_async_wait_all();
+  } while (PERSIST && (tile += (int)gridDim.x) < ntiles);
   if (failed && tid == 0) {  // failed is uniform across the CTA
     atomicAdd(&counters[2], 1ull);
     // the last round, if it is still in flight, with the full limit
@@ -496,7 +383,7 @@ __global__ void __launch_bounds__(kTileX, tc_rows(TY) == 1 ? 5 : 3)
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  if (warp == 0) tc::tmem_dealloc(tmem, kCols);
+  if (warp == 0) tc::tmem_dealloc(tmem, kH);
 }
 
 }  // namespace lbm

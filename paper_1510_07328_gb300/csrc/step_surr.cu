@@ -58,7 +58,9 @@ template <class T, int TY, bool PERSIST>
 static int prepare_one() {
   auto k = stream_collide_surr_tc<T, TY, PERSIST>;
   constexpr int R = tc_rows(TY);
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem(R)) != cudaSuccess) return 0;
+  constexpr int smem_k = tc_smem(R);
+  constexpr int cols = R * kH;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_k) != cudaSuccess) return 0;
   if (cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess) return 0;
   cudaFuncAttributes fa;
   if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) return 0;
@@ -69,8 +71,8 @@ static int prepare_one() {
   if (cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) return 0;
   const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;  // allocated per warp in units of 256
   const int by_regs = regs_sm / (warp_regs * (kTileX / 32));
-  const int by_smem = smem_sm / ((int)fa.sharedSizeBytes + tc_smem(R) + reserved);
-  const int by_tmem = 512 / (R * kH);
+  const int by_smem = smem_sm / ((int)fa.sharedSizeBytes + smem_k + reserved);
+  const int by_tmem = 512 / cols;
   return std::max(0, std::min(std::min(by_regs, by_smem), std::min(by_tmem, 2048 / kTileX)));
 }
 

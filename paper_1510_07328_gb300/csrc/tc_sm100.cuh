@@ -109,6 +109,18 @@ __device__ __forceinline__ void tmem_ld64_pack16(uint32_t taddr, uint32_t (&r)[3
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 32 consecutive 16-bit columns of this thread's TMEM lane, packed in pairs
+// as tmem_ld64_pack16 (half the registers live at a time).
+__device__ __forceinline__ void tmem_ld32_pack16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.pack::16b.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // 4 consecutive FP32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
   uint32_t r[4];
@@ -127,6 +139,35 @@ __device__ __forceinline__ uint32_t silu2_packed(uint32_t h) {
   const __half2 hv = *reinterpret_cast<const __half2*>(&h), tv = *reinterpret_cast<const __half2*>(&t);
   const __half2 s = __hfma2(hv, tv, hv);
   return *reinterpret_cast<const uint32_t*>(&s);
+}
+
+// SiLU of a packed FP16 pair of halved arguments h = z/2 on the FMA pipe:
+//   silu(z) = relu(z) + q(|h|),  q(s) = s tanh(s) - s,
+// with q by its degree-6 minimax polynomial in t = min(|h|, 4.5) (2/4.5) - 1
+// (Lawson's algorithm; fit_silu_poly.py prints the coefficients), evaluated
+// by Horner's rule in packed FP16.  Error within 3.6e-3 of max(1, |silu(z)|)
+// (the MUFU path: 1.1e-3), including the clamp's tail |q(4.5)| = 1.1e-3.
+// Constants: FP16 bit patterns, the same value in both halves.
+constexpr uint32_t kSiluClamp = 0x44804480u, kSiluScale = 0x371C371Cu, kSiluMinus1 = 0xBC00BC00u,
+                   kSiluTwo = 0x40004000u;
+// coefficients of t^6 .. t^0
+constexpr uint32_t kSiluC6 = 0x31AD31ADu, kSiluC5 = 0xB747B747u, kSiluC4 = 0x32383238u, kSiluC3 = 0x349D349Du,
+                   kSiluC2 = 0xB534B534u, kSiluC1 = 0x313A313Au, kSiluC0 = 0xAA04AA04u;
+
+__device__ __forceinline__ __half2 h2bits(uint32_t b) { return *reinterpret_cast<const __half2*>(&b); }
+
+__device__ __forceinline__ uint32_t silu2_poly(uint32_t hu) {
+  const __half2 h = h2bits(hu);
+  const __half2 s = __hmin2(__habs2(h), h2bits(kSiluClamp));
+  const __half2 t = __hfma2(s, h2bits(kSiluScale), h2bits(kSiluMinus1));
+  __half2 p = __hfma2(h2bits(kSiluC6), t, h2bits(kSiluC5));
+  p = __hfma2(p, t, h2bits(kSiluC4));
+  p = __hfma2(p, t, h2bits(kSiluC3));
+  p = __hfma2(p, t, h2bits(kSiluC2));
+  p = __hfma2(p, t, h2bits(kSiluC1));
+  p = __hfma2(p, t, h2bits(kSiluC0));
+  const __half2 o = __hfma2(__hmax2(h, h2bits(0u)), h2bits(kSiluTwo), p);
+  return *reinterpret_cast<const uint32_t*>(&o);
 }
 
 }  // namespace tc
