@@ -58,8 +58,14 @@ typedef enum {
  * dimensions").  FD: J_2 from the energy moment, J_4 from the inverted x.
  * FD_T0: the theta = 0 closure of Sect. "Numerical simulations for electrons
  * in metals", J_N = 1 + 2/(N + D) constant.  MB: J_N = 1, the Hermite D2Q9
- * limit. */
-typedef enum { LBM_STAT_FD = 0, LBM_STAT_FD_T0 = 1, LBM_STAT_MB = 2 } lbm_stat;
+ * limit.  FT: FD statistics at a temperature theta fixed per problem, the
+ * literal reading of the moment update after the LBGK equation (which names
+ * only I_0 and u_0): x follows from the density alone, n = 2 pi theta
+ * f_1(x), and J_2, J_4 are the FD values at that x; energy is not conserved
+ * by a collision.  theta = n_ref t_ref/(2 pi) of each problem (so n_ref and
+ * t_ref are required at every precision).  d2v9 with the exact inversion and
+ * without obstacles or forces only. */
+typedef enum { LBM_STAT_FD = 0, LBM_STAT_FD_T0 = 1, LBM_STAT_MB = 2, LBM_STAT_FT = 3 } lbm_stat;
 
 /* Population storage.  F64: f itself in FP64, all arithmetic FP64.
  * F32_DEV / BF16_DEV: the deviation g_a = f_a - W_a^ref from a per-problem
@@ -180,7 +186,9 @@ typedef struct {
  *  n; u_0 = (ux, uy) in lattice units; T = theta and mu in the paper's
  *  dimensionless units (m = k_B = hbar = 1); t = T/T_F.  For LBM_STAT_FD_T0,
  *  T = t = 0 and mu = T_F, the theta = 0 chemical potential at density n
- *  (n/(2 pi) on d2v9, n^2/8 on d1v3); for LBM_STAT_MB, T, mu, t are NaN.
+ *  (n/(2 pi) on d2v9, n^2/8 on d1v3); for LBM_STAT_MB, T, mu, t are NaN;
+ *  for LBM_STAT_FT, T = theta, t = 2 pi theta/n and mu = theta x(n), with no
+ *  clamped cells counted.
  *  On d1v3 uy is 0 and diag.sum_E = sum of f e^2.
  * out_on_device != 0: the pointers are device memory and the call is
  * asynchronous; otherwise host memory and the call synchronises.  diag may be
@@ -354,7 +362,7 @@ lbm_status lbm_surrogate_wait_limit(lbm_ctx* ctx, int32_t polls);
  *        leaves them out.
  * stat:  lbm_stat; for LBM_STAT_FD a cell counts as clamped when its finite
  *        J_2 lies outside the inversion's interval, the rule of lbm_moments;
- *        otherwise the count is 0.
+ *        for the other closures (no inversion) the count is 0.
  * out:   device pointer to 6 doubles, written in stream order: sum n,
  *        sum j_x, sum j_y, sum E, clamped count, non-finite count (the fields
  *        of lbm_diag).

@@ -59,7 +59,7 @@ static __global__ void ref_kernel(ProbDev* probs, int nprob, int stat, int dim) 
     return;
   }
   double J2, J4;
-  if (stat == STAT_FD) {
+  if (stat == STAT_FD || stat == STAT_FT) {
     if (P.n_ref > 0.0) closure_from_t<STAT_FD>(P.t_ref, J2, J4); else J2 = 1.5;
   } else if (stat == STAT_T0) {
     J2 = FixedJ<STAT_T0>::j2;
@@ -79,6 +79,7 @@ static __global__ void ref_kernel(ProbDev* probs, int nprob, int stat, int dim) 
   P.f.wref[0] = (float)w0;
   P.f.wref[1] = (float)ws;
   P.f.wref[2] = (float)wl;
+  P.f.two_pi_theta = (float)(2.0 * kPi * P.theta);
 }
 
 
@@ -234,12 +235,14 @@ void launch_init_t(lbm_ctx* c, const ProbDev& P, const InitDesc& d) {
     switch (c->stat) {
       case LBM_STAT_FD: init_dev_kernel<T, STAT_FD><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
       case LBM_STAT_FD_T0: init_dev_kernel<T, STAT_T0><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
+      case LBM_STAT_FT: init_dev_kernel<T, STAT_FT><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
       default: init_dev_kernel<T, STAT_MB><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
     }
   } else {
     switch (c->stat) {
       case LBM_STAT_FD: init_kernel<T, STAT_FD><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
       case LBM_STAT_FD_T0: init_kernel<T, STAT_T0><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
+      case LBM_STAT_FT: init_kernel<T, STAT_FT><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
       default: init_kernel<T, STAT_MB><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
     }
   }
@@ -257,6 +260,7 @@ void launch_moments_p(lbm_ctx* c, const ProbDev& P, double* o[6], unsigned g) {
   switch (c->stat) {
     case LBM_STAT_FD: launch_moments_t<T, STAT_FD>(c, P, o, g); break;
     case LBM_STAT_FD_T0: launch_moments_t<T, STAT_T0>(c, P, o, g); break;
+    case LBM_STAT_FT: launch_moments_t<T, STAT_FT>(c, P, o, g); break;
     default: launch_moments_t<T, STAT_MB>(c, P, o, g); break;
   }
 }
@@ -300,12 +304,12 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
   *out = nullptr;
   if (p->dim != 1 && p->dim != 2)
     return fail(nullptr, LBM_EUNSUPPORTED, "lbm_create: dim must be 1 (d1v3) or 2 (d2v9)");
-  if (p->dim == 1 && p->stat == LBM_STAT_FD)
+  if (p->dim == 1 && (p->stat == LBM_STAT_FD || p->stat == LBM_STAT_FT))
     return fail(nullptr, LBM_EUNSUPPORTED,
                 "lbm_create: d1v3 has no finite-temperature closure (n, j and E fix its three populations); "
                 "use LBM_STAT_FD_T0 or LBM_STAT_MB");
   if (p->order != 3) return fail(nullptr, LBM_EUNSUPPORTED, "lbm_create: only order K = 3 is implemented");
-  if (p->stat < 0 || p->stat > 2) return fail(nullptr, LBM_EINVAL, "lbm_create: bad stat");
+  if (p->stat < 0 || p->stat > 3) return fail(nullptr, LBM_EINVAL, "lbm_create: bad stat");
   if (p->prec < 0 || p->prec > 2) return fail(nullptr, LBM_EINVAL, "lbm_create: bad prec");
   if (p->inv != LBM_INV_EXACT && p->inv != LBM_INV_SURROGATE) return fail(nullptr, LBM_EINVAL, "lbm_create: bad inv");
   if (p->inv == LBM_INV_SURROGATE && (p->prec == LBM_F64 || p->stat != LBM_STAT_FD || p->dim != 2))
@@ -320,9 +324,9 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
     if (!(q.tau > 0.5) || !std::isfinite(q.tau)) return fail(nullptr, LBM_EINVAL, "lbm_create: tau must be > 1/2");
     if ((q.bc_x != 0 && q.bc_x != 1) || (q.bc_y != 0 && q.bc_y != 1))
       return fail(nullptr, LBM_EINVAL, "lbm_create: bad boundary kind");
-    if (p->prec != LBM_F64) {
+    if (p->prec != LBM_F64 || p->stat == LBM_STAT_FT) {  // FT: theta = n_ref t_ref/(2 pi) at any precision
       if (!(q.n_ref > 0.0) || !std::isfinite(q.n_ref)) return fail(nullptr, LBM_EINVAL, "lbm_create: n_ref must be > 0");
-      if (p->stat == LBM_STAT_FD && !valid_t(q.t_ref))
+      if ((p->stat == LBM_STAT_FD || p->stat == LBM_STAT_FT) && !valid_t(q.t_ref))
         return fail(nullptr, LBM_EINVAL, "lbm_create: t_ref must lie in [1e-3, 10]");
     }
   }
@@ -349,6 +353,7 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
     d.base = base;
     d.tau = q.tau;
     d.omega = 1.0 / q.tau;
+    d.theta = p->stat == LBM_STAT_FT ? q.n_ref * q.t_ref / (2.0 * kPi) : 0.0;
     d.n_ref = p->prec == LBM_F64 ? 0.0 : q.n_ref;
     d.t_ref = p->prec == LBM_F64 ? 0.0 : q.t_ref;
     base += (int64_t)d.pitch * q.ny;
@@ -870,6 +875,8 @@ lbm_status porous_allowed(lbm_ctx* ctx, const char* who) {
   if (ctx->dim != 2) return fail(ctx, LBM_EUNSUPPORTED, std::string(who) + ": obstacles and forces need d2v9");
   if (ctx->inv != LBM_INV_EXACT)
     return fail(ctx, LBM_EUNSUPPORTED, std::string(who) + ": obstacles and forces need the exact inversion");
+  if (ctx->stat == LBM_STAT_FT)
+    return fail(ctx, LBM_EUNSUPPORTED, std::string(who) + ": obstacles and forces are not built for LBM_STAT_FT");
   return LBM_OK;
 }
 

@@ -104,7 +104,7 @@ __device__ __forceinline__ void relax_store_dev(const ProbDev& P, const float g[
   const float dn = m.dn, X = m.X, ux = m.ux, uy = m.uy, u2 = m.u2;
   // weight changes against the reference (exact algebra, see header comment)
   float dW0, dWs, dWl;
-  if (STAT == STAT_FD) {
+  if (STAT == STAT_FD || STAT == STAT_FT) {  // X of the closure's J_2 (see header)
     dW0 = dn * (1.0f / 6.0f) + (5.0f / 6.0f) * X;
     dWs = (dn - X) * (1.0f / 6.0f);
     dWl = 0.25f * dWs;
@@ -152,12 +152,20 @@ __device__ __forceinline__ void relax_store_dev(const ProbDev& P, const float g[
 template <class T, int STAT>
 __device__ __forceinline__ void collide_store_dev(const ProbDev& P, const float g[9], T* __restrict__ fout,
                                                   int64_t plane, int off, const InvLimitsF& L) {
-  const CellMom m = dev_moments(P, g);
+  CellMom m = dev_moments(P, g);
   float J2, J4;
   if (STAT == STAT_FD) {
     J2 = 1.5f - m.delta;
     float xx;
     J4 = j4_from_delta_f(m.delta, L, &xx);
+  } else if (STAT == STAT_FT) {
+    // fixed theta: the cell's t = 2 pi theta/n; delta = 3/2 - J_2(t) without
+    // subtraction, and X = (2/3)(n delta - n_ref delta_ref) for the weights
+    float delta;
+    closure_dev_from_t(P.f.two_pi_theta * m.in, delta, J4);
+    m.delta = delta;
+    m.X = (m.n * delta - P.f.ndelta_ref) * (2.0f / 3.0f);
+    J2 = 1.5f - delta;
   } else {
     J2 = (float)FixedJ<STAT>::j2;
     J4 = (float)FixedJ<STAT>::j4;

@@ -15,7 +15,9 @@
 
 namespace lbm {
 
-enum { STAT_FD = 0, STAT_T0 = 1, STAT_MB = 2 };
+// FD: J_2 from the energy moment, x by inversion; T0: theta = 0 constants;
+// MB: Hermite limit; FT: theta fixed per problem, x from the density alone.
+enum { STAT_FD = 0, STAT_T0 = 1, STAT_MB = 2, STAT_FT = 3 };
 enum { BC_PERIODIC = 0, BC_BOUNCEBACK = 1 };
 
 constexpr int kTileX = 128;      // cells of one row handled by one CTA (one per thread)
@@ -28,10 +30,12 @@ struct ProbDev {
   double n_ref, t_ref;               // deviation reference state (n_ref = 0: absolute storage)
   double j2_ref, ndelta_ref;         // J_2(t_ref), n_ref (3/2 - J_2(t_ref))
   double wref[9];                    // W_a^ref = w_a(J_2(t_ref)) n_ref
+  double theta;                      // fixed-theta closure: theta = n_ref t_ref/(2 pi) of the problem
   struct {
     float omega, n_ref, ndelta_ref;
     float wref[3];  // rest, short, long
     float fx, fy;
+    float two_pi_theta;  // 2 pi theta (fixed-theta closure)
   } f;              // FP32 copies for the reduced-precision step
   const uint8_t* solid;              // obstacle mask indexed like the cells (nonzero: solid), or null
   double fx, fy;                     // constant body force per cell and step
@@ -103,7 +107,7 @@ __device__ __forceinline__ void feq_f64(double n, double ux, double uy, double J
 // J_2, J_4 of a state given by t (FD) or by the closure.
 template <int STAT>
 __device__ __forceinline__ void closure_from_t(double t, double& J2, double& J4) {
-  if (STAT == STAT_FD) {
+  if (STAT == STAT_FD || STAT == STAT_FT) {
     const FD5 f = fd_eval(x_of_t(t));
     J2 = j2_of(f);
     J4 = j4_of(f);
@@ -243,6 +247,9 @@ __global__ void __launch_bounds__(kTileX) stream_collide_f64(const double* __res
         int cl;
         double xx;
         J4 = j4_fp64(J2, L, Lf, &xx, &cl);
+      } else if (STAT == STAT_FT) {
+        // fixed theta: 2 pi theta f_1(x) = n, so the cell's t = 1/f_1(x) = 2 pi theta/n
+        closure_from_t<STAT_FT>(2.0 * kPi * P.theta * in, J2, J4);
       } else {
         J2 = FixedJ<STAT>::j2;
         J4 = FixedJ<STAT>::j4;
@@ -383,6 +390,12 @@ __global__ void __launch_bounds__(kMomThreads) moments_kernel(const T* __restric
       }
       theta = n * t / (2.0 * kPi);     // theta = n t/(2 pi), T_F = n/(2 pi)
       mu = theta * xx;
+    } else if (STAT == STAT_FT) {
+      // fixed theta: t = 2 pi theta/n, x = ln(e^{1/t} - 1) = a + ln(1 - e^{-a}), a = 1/t
+      theta = P.theta;
+      t = 2.0 * kPi * theta / n;
+      const double a = 1.0 / t;
+      mu = theta * (a + log(-expm1(-a)));
     } else if (STAT == STAT_T0) {
       theta = 0.0; t = 0.0; mu = n / (2.0 * kPi);
     } else {

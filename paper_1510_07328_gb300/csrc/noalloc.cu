@@ -192,7 +192,7 @@ extern "C" lbm_status lbm_conservation_sums_static(const double* f, int32_t nx, 
   if (nx < 1 || ny < 1) return static_fail(LBM_EINVAL, "nx and ny must be >= 1");
   const int64_t cells = (int64_t)nx * ny;
   if (cells > kStaticMaxCells) return static_fail(LBM_EINVAL, "", (long long)cells);
-  if (stat < LBM_STAT_FD || stat > LBM_STAT_MB) return static_fail(LBM_EINVAL, "bad stat");
+  if (stat < LBM_STAT_FD || stat > LBM_STAT_FT) return static_fail(LBM_EINVAL, "bad stat");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return static_fail(LBM_ECUDA, "cudaGetDevice failed");
   if (dev < 0 || dev >= kMaxDevices) return static_fail(LBM_EUNSUPPORTED, "device index above 63");
@@ -210,7 +210,9 @@ extern "C" lbm_status lbm_conservation_sums_static(const double* f, int32_t nx, 
     case LBM_STAT_FD_T0:
       static_sums_kernel<LBM_STAT_FD_T0><<<blocks, kStaticThreads, 0, s>>>(f, cells, solid, limits, partials);
       break;
-    default: static_sums_kernel<LBM_STAT_MB><<<blocks, kStaticThreads, 0, s>>>(f, cells, solid, limits, partials); break;
+    default:  // MB and FT: no inversion, nothing clamped
+      static_sums_kernel<LBM_STAT_MB><<<blocks, kStaticThreads, 0, s>>>(f, cells, solid, limits, partials);
+      break;
   }
   static_final_kernel<<<1, 256, 0, s>>>(partials, blocks, out);
   const cudaError_t e = cudaGetLastError();

@@ -29,6 +29,7 @@ void launch_step_f64(int stat, int rows, unsigned grid, cudaStream_t s, const St
   switch (stat) {
     case STAT_FD: by_rows<STAT_FD>(rows, grid, s, a); break;
     case STAT_T0: by_rows<STAT_T0>(rows, grid, s, a); break;
+    case STAT_FT: by_rows<STAT_FT>(rows, grid, s, a); break;
     default: by_rows<STAT_MB>(rows, grid, s, a); break;
   }
 }

@@ -19,13 +19,13 @@ import numpy as np
 from . import build as _build
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ETIMEOUT, LBM_EUNSUPPORTED = range(6)
-LBM_STAT_FD, LBM_STAT_FD_T0, LBM_STAT_MB = range(3)
+LBM_STAT_FD, LBM_STAT_FD_T0, LBM_STAT_MB, LBM_STAT_FT = range(4)
 LBM_F64, LBM_F32_DEV, LBM_BF16_DEV = range(3)
 LBM_INV_EXACT, LBM_INV_SURROGATE = range(2)
 LBM_BC_PERIODIC, LBM_BC_BOUNCEBACK = range(2)
 LBM_INIT_HALF, LBM_INIT_QUADRANT, LBM_INIT_FIELD = range(3)
 
-STAT = {"fd": LBM_STAT_FD, "t0": LBM_STAT_FD_T0, "mb": LBM_STAT_MB}
+STAT = {"fd": LBM_STAT_FD, "t0": LBM_STAT_FD_T0, "mb": LBM_STAT_MB, "ft": LBM_STAT_FT}
 PREC = {"f64": LBM_F64, "f32": LBM_F32_DEV, "bf16": LBM_BF16_DEV}
 BC = {"periodic": LBM_BC_PERIODIC, "bounceback": LBM_BC_BOUNCEBACK}
 
@@ -392,13 +392,16 @@ class Lattice:
     """One context over a list of problems (``inputs.Problem`` objects)."""
 
     def __init__(self, problems, stat="fd", prec="f64", stream=None, t_ref=None, n_ref=None, inv="exact",
-                 surrogate=None, dim=2, engine=None):
+                 surrogate=None, dim=2, engine=None, theta=None):
+        """theta: the fixed temperature of stat "ft" (sets t_ref = 2 pi theta/n_ref)."""
         self.problems = list(problems)
         self.q = 9 if dim == 2 else 3
         descs = []
         for p in self.problems:
-            tr = t_ref if t_ref is not None else float(np.median(p.t)) if stat == "fd" else 0.05
+            tr = t_ref if t_ref is not None else float(np.median(p.t)) if stat in ("fd", "ft") else 0.05
             nr = n_ref if n_ref is not None else float(np.mean(p.n))
+            if theta is not None:
+                tr = 2.0 * np.pi * theta / nr
             descs.append(dict(nx=p.nx, ny=p.ny, tau=p.tau, bc_x=p.bc_x, bc_y=p.bc_y, n_ref=nr,
                               t_ref=min(max(tr, 1e-3), 10.0)))
         self.ctx = lbm_create(descs, stat, prec, inv=inv, stream=stream, dim=dim)

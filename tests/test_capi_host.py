@@ -130,6 +130,28 @@ def test_create_rejects_d1v3_misuse(lib):
     assert lib.LIB.lbm_create(C.byref(par), None, C.byref(ctx)) == lib.LBM_EUNSUPPORTED
 
 
+def test_create_rejects_fixed_theta_misuse(lib):
+    """The fixed-theta closure (LBM_STAT_FT) needs d2v9, the exact inversion,
+    and theta = n_ref t_ref/(2 pi) from a positive n_ref and t_ref in
+    [1e-3, 10] at every precision; every check happens before any CUDA call."""
+    import ctypes as C
+
+    ft = lib.STAT["ft"]
+    ctx = C.c_void_p()
+    arr = (lib.lbm_problem * 1)(lib.lbm_problem(64, 1, 0.8, 0, 0, 1.0, 0.05))
+    par = lib.lbm_params(1, 3, ft, 0, 0, 1, arr)  # d1v3
+    assert lib.LIB.lbm_create(C.byref(par), None, C.byref(ctx)) == lib.LBM_EUNSUPPORTED
+    arr = (lib.lbm_problem * 1)(lib.lbm_problem(64, 4, 0.8, 0, 0, 1.0, 0.05))
+    par = lib.lbm_params(2, 3, ft, 1, 1, 1, arr)  # learned inversion
+    assert lib.LIB.lbm_create(C.byref(par), None, C.byref(ctx)) == lib.LBM_EUNSUPPORTED
+    for n_ref, t_ref in ((0.0, 0.05), (1.0, 0.0), (1.0, 20.0)):
+        arr = (lib.lbm_problem * 1)(lib.lbm_problem(64, 4, 0.8, 0, 0, n_ref, t_ref))
+        par = lib.lbm_params(2, 3, ft, 0, 0, 1, arr)  # FP64 storage: still required
+        assert lib.LIB.lbm_create(C.byref(par), None, C.byref(ctx)) == lib.LBM_EINVAL
+    par = lib.lbm_params(2, 3, 4, 0, 0, 1, arr)  # no closure 4
+    assert lib.LIB.lbm_create(C.byref(par), None, C.byref(ctx)) == lib.LBM_EINVAL
+
+
 @pytest.mark.parametrize("kw,msg", [
     (dict(stat="FD"), "closure"),
     (dict(prec="fp32"), "storage"),
