@@ -160,8 +160,11 @@ def test_paper_porous_experiment_ohms_law(L):
     """The paper's sample (30 discs of radius 3 in 700 x 150, periodic,
     tau = 0.7) under forces F_k = k F_0, k = 1..4, as four problems of one
     context: at steady state the mean fluid velocity along the force is
-    proportional to it.  The paper fits a = 1.00013 to the values normalised
-    by the lowest; here |a - 1| < 1e-4.
+    proportional to it.  The paper fits a = 1.00013 +- 0.00001 to the values
+    normalised by the lowest (Fig. 2 caption); here |a - 1| < 2e-4, a band
+    that holds the paper's own fit and rejects any nonlinear response (at
+    F_0 = 2e-8 weak inertia already bends the line by 2e-3).  The obstacle
+    positions are not published, so the paper's exact slope cannot be pinned.
     Closure: Maxwell-Boltzmann.  At tau = 0.7 the theta = 0 closure on d2v9 is
     linearly unstable (growth 1.14 per step), and the FD energy closure at
     T/T_F = 0.5 grows once the flow around the obstacles is non-uniform (no
@@ -191,4 +194,5 @@ def test_paper_porous_experiment_ohms_law(L):
     a = float((Fn * un).sum() / (Fn * Fn).sum())
     print(f"mean velocity / F: {us / (Fn * F0)}, fit a = {a:.7f}")
     assert np.all(us > 0)
-    assert abs(a - 1.0) < 1e-4
+    assert abs(1.00013 - 1.0) < 2e-4  # the paper's printed fit lies inside the band
+    assert abs(a - 1.0) < 2e-4
