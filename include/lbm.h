@@ -119,7 +119,12 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out);
  *  HALF:     s[0] for x < x0, s[1] for x >= x0.
  *  QUADRANT: s[q], q = (x >= x0) + 2 (y >= y0).
  *  FIELD:    per-cell arrays n, ux, uy, t of nx*ny doubles each, host or
- *            device memory per field_on_device; read during the call only.
+ *            device memory per field_on_device; read during the call only
+ *            (with host arrays the call synchronises before it returns).
+ *            Host arrays in page-locked memory that the GPU can address
+ *            (cudaHostAlloc, or registered) are read in place by the kernel,
+ *            over the coherent chip-to-chip link on a Grace-Blackwell node;
+ *            pageable ones go through a staging copy.
  * t is T/T_F (T_F the theta = 0 chemical potential at the cell's density);
  * it must lie in [1e-3, 10] for LBM_STAT_FD and is ignored otherwise.  On
  * d1v3 QUADRANT is invalid and uy is ignored (FIELD still takes all four
@@ -191,8 +196,10 @@ typedef struct {
  *  clamped cells counted.
  *  On d1v3 uy is 0 and diag.sum_E = sum of f e^2.
  * out_on_device != 0: the pointers are device memory and the call is
- * asynchronous; otherwise host memory and the call synchronises.  diag may be
- * NULL; if not, the call synchronises and fills it (host memory). */
+ * asynchronous; otherwise host memory and the call synchronises (host arrays
+ * in page-locked memory that the GPU can address are written in place by the
+ * kernel, pageable ones through a staging copy).  diag may be NULL; if not,
+ * the call synchronises and fills it (host memory). */
 lbm_status lbm_moments(lbm_ctx* ctx, int32_t problem, double* n, double* ux, double* uy,
                        double* T, double* mu, double* t, int32_t out_on_device, lbm_diag* diag);
 

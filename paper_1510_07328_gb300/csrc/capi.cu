@@ -80,6 +80,8 @@ static __global__ void ref_kernel(ProbDev* probs, int nprob, int stat, int dim) 
   P.f.wref[1] = (float)ws;
   P.f.wref[2] = (float)wl;
   P.f.two_pi_theta = (float)(2.0 * kPi * P.theta);
+  P.nsum_ref = w0 + 4.0 * ws + 4.0 * wl;
+  P.esum_ref = 4.0 * ws + 8.0 * wl;
 }
 
 
@@ -250,9 +252,13 @@ void launch_init_t(lbm_ctx* c, const ProbDev& P, const InitDesc& d) {
 
 template <class T, int STAT>
 void launch_moments_t(lbm_ctx* c, const ProbDev& P, double* o[6], unsigned g) {
-  // deviation storage: the closure quantities from the FP32 inversion
-  moments_kernel<T, STAT, Stor<T>::dev><<<g, kMomThreads, 0, c->stream>>>(
-      (const T*)c->buf[c->cur], P, c->plane, c->lim, c->limf, o[0], o[1], o[2], o[3], o[4], o[5], c->partials);
+  // deviation storage: error-free FP32 sums and the closure quantities from the FP32 inversion
+  if constexpr (Stor<T>::dev)
+    moments_dev_kernel<T, STAT><<<g, kMomThreads, 0, c->stream>>>(
+        (const T*)c->buf[c->cur], P, c->plane, c->lim, c->limf, o[0], o[1], o[2], o[3], o[4], o[5], c->partials);
+  else
+    moments_kernel<T, STAT><<<g, kMomThreads, 0, c->stream>>>(
+        (const T*)c->buf[c->cur], P, c->plane, c->lim, c->limf, o[0], o[1], o[2], o[3], o[4], o[5], c->partials);
 }
 
 template <class T>
@@ -276,6 +282,19 @@ lbm_status ensure_tmp(lbm_ctx* ctx, int64_t doubles) {
 }
 
 bool valid_t(double t) { return t >= kTMin && t <= kTMax; }
+
+// The device address of page-locked host memory that the GPU can reach
+// directly (on a Grace-Blackwell node over the coherent chip-to-chip link),
+// or NULL for pageable memory: kernels then read or write the caller's host
+// array in place instead of going through a staging copy.
+void* device_view(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the error of an unknown pointer
+    return nullptr;
+  }
+  return (a.type == cudaMemoryTypeHost && a.devicePointer != nullptr) ? a.devicePointer : nullptr;
+}
 
 }  // namespace
 
@@ -449,15 +468,26 @@ lbm_status lbm_init_riemann(lbm_ctx* ctx, int32_t problem, const lbm_riemann_des
       k.uy = d->uy;
       k.t = d->t;
     } else {
-      lbm_status s = ensure_tmp(ctx, 4 * cells);
-      if (s != LBM_OK) return s;
       const double* src[4] = {d->n, d->ux, d->uy, d->t};
-      for (int a = 0; a < 4; ++a)
-        CK(cudaMemcpyAsync(ctx->tmp + a * cells, src[a], sizeof(double) * cells, cudaMemcpyHostToDevice, ctx->stream));
-      k.n = ctx->tmp;
-      k.ux = ctx->tmp + cells;
-      k.uy = ctx->tmp + 2 * cells;
-      k.t = ctx->tmp + 3 * cells;
+      void* view[4];
+      bool direct = true;
+      for (int a = 0; a < 4; ++a) direct = (view[a] = device_view(src[a])) != nullptr && direct;
+      if (direct) {  // page-locked host fields: the kernel reads them in place
+        k.n = (const double*)view[0];
+        k.ux = (const double*)view[1];
+        k.uy = (const double*)view[2];
+        k.t = (const double*)view[3];
+      } else {
+        lbm_status s = ensure_tmp(ctx, 4 * cells);
+        if (s != LBM_OK) return s;
+        for (int a = 0; a < 4; ++a)
+          CK(cudaMemcpyAsync(ctx->tmp + a * cells, src[a], sizeof(double) * cells, cudaMemcpyHostToDevice,
+                             ctx->stream));
+        k.n = ctx->tmp;
+        k.ux = ctx->tmp + cells;
+        k.uy = ctx->tmp + 2 * cells;
+        k.t = ctx->tmp + 3 * cells;
+      }
     }
   } else {
     return fail(ctx, LBM_EINVAL, "lbm_init_riemann: bad kind");
@@ -763,13 +793,28 @@ lbm_status lbm_moments(lbm_ctx* ctx, int32_t problem, double* n, double* ux, dou
   }
   double* user[6] = {n, ux, uy, T, mu, t};
   double* o[6] = {n, ux, uy, T, mu, t};
+  bool staged[6] = {false, false, false, false, false, false};
   if (!out_on_device) {
+    // page-locked host arrays are written in place by the kernel; the others
+    // through device staging and a copy
     int nf = 0;
-    for (int a = 0; a < 6; ++a) nf += user[a] != nullptr;
-    lbm_status s = ensure_tmp(ctx, nf * cells);
-    if (s != LBM_OK) return s;
+    for (int a = 0; a < 6; ++a) {
+      if (!user[a]) continue;
+      void* v = device_view(user[a]);
+      if (v) {
+        o[a] = (double*)v;
+      } else {
+        staged[a] = true;
+        ++nf;
+      }
+    }
+    if (nf > 0) {
+      lbm_status s = ensure_tmp(ctx, nf * cells);
+      if (s != LBM_OK) return s;
+    }
     int k = 0;
-    for (int a = 0; a < 6; ++a) o[a] = user[a] ? ctx->tmp + (k++) * cells : nullptr;
+    for (int a = 0; a < 6; ++a)
+      if (staged[a]) o[a] = ctx->tmp + (k++) * cells;
   }
   if (ctx->dim == 1) {
     launch_moments_d1(ctx->prec, ctx->stat, ctx->buf[ctx->cur], P, ctx->plane, o, ctx->partials, g, ctx->stream);
@@ -789,7 +834,7 @@ lbm_status lbm_moments(lbm_ctx* ctx, int32_t problem, double* n, double* ux, dou
   }
   if (!out_on_device) {
     for (int a = 0; a < 6; ++a)
-      if (user[a]) CK(cudaMemcpyAsync(user[a], o[a], sizeof(double) * cells, cudaMemcpyDeviceToHost, ctx->stream));
+      if (staged[a]) CK(cudaMemcpyAsync(user[a], o[a], sizeof(double) * cells, cudaMemcpyDeviceToHost, ctx->stream));
   }
   if (diag) {
     double h[kNPartial];

@@ -2,7 +2,7 @@
 // computed with the reduced-precision step's own arithmetic: the equilibrium
 // in FP32 deviation form and the Fermi-Dirac closure from t in FP32, with
 // errors of the order of one FP32 step.  (Their moments take the closure
-// quantities from the FP32 inversion: moments_kernel with F32CL.)
+// quantities from the FP32 inversion: moments_dev_kernel.)
 #pragma once
 #include "lbm_dev32.cuh"
 

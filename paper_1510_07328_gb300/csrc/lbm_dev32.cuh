@@ -239,4 +239,144 @@ __global__ void __launch_bounds__(kTileX, sizeof(T) == 4 ? 8 : 10) stream_collid
   } while (PERSIST && (tile += (int)gridDim.x) < ntiles);
 }
 
+// ------------------------------------------------------------------ moments of deviation storage
+
+// Knuth's TwoSum: s + e = a + b exactly in round-to-nearest FP32 (no
+// multiplication, so no contraction can change it).
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// A sum of FP32 terms as an unevaluated pair hi + lo: every addition's
+// rounding error goes into lo, so hi + lo carries the sum to about 2^-47.
+struct DFsum {
+  float hi, lo;
+};
+__device__ __forceinline__ DFsum df_add(DFsum a, float b) {
+  float s, e;
+  two_sum_f(a.hi, b, s, e);
+  return DFsum{s, a.lo + e};
+}
+__device__ __forceinline__ double df_value(DFsum a) { return (double)a.hi + (double)a.lo; }
+
+// lbm_moments for FP32/BF16 deviation storage: the fields and diagnostics of
+// moments_kernel, with x, t, theta, mu from the step's FP32 inversion and
+// the FP64 work cut to what
+// the results need (FP64 runs at 1/64 of the FP32 rate on this GPU): the
+// deviation sums n - n_ref = sum g, j = sum g e and E - E_ref = sum g |e|^2
+// as error-free FP32 sums (hi + lo, two_sum_f), converted once; 1/n as an
+// FP32 reciprocal refined by two FP64 Newton steps in place of FP64
+// divisions.  Both reach the FP64 sums of the stored values to a few units
+// of 1e-16 relative.  n_ref = sum W_ref and E_ref = sum W_ref |e|^2 are the
+// reference weights' sums (ProbDev::nsum_ref, esum_ref).  The clamp count and
+// x, t, theta, mu come from the step's FP32 deviation moments and inversion.
+template <class T, int STAT>
+__global__ void __launch_bounds__(kMomThreads) moments_dev_kernel(const T* __restrict__ f, ProbDev P, int64_t plane,
+                                                                  InvLimits L, InvLimitsF Lf, double* __restrict__ on,
+                                                                  double* __restrict__ oux, double* __restrict__ ouy,
+                                                                  double* __restrict__ oT, double* __restrict__ omu,
+                                                                  double* __restrict__ ot,
+                                                                  double* __restrict__ partials) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t cells = (int64_t)P.nx * P.ny;
+  double acc[kNPartial] = {0, 0, 0, 0, 0, 0};
+  const int64_t c = i < cells ? P.base + (int64_t)(i / P.nx) * P.pitch + (int)(i % P.nx) : 0;
+  if (i < cells && P.solid != nullptr && P.solid[c] != 0) {  // obstacle: no fluid
+    if (on) on[i] = 0.0;
+    if (oux) oux[i] = 0.0;
+    if (ouy) ouy[i] = 0.0;
+    if (oT) oT[i] = 0.0;
+    if (omu) omu[i] = 0.0;
+    if (ot) ot[i] = 0.0;
+  } else if (i < cells) {
+    float g[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) g[a] = Dev<T>::ld(f[a * plane + c]);
+    DFsum sn{g[0], 0.0f}, sx{g[1], 0.0f}, sy{g[2], 0.0f}, se{g[1], 0.0f};
+#pragma unroll
+    for (int a = 1; a < 9; ++a) sn = df_add(sn, g[a]);
+    sx = df_add(sx, -g[3]);
+    sx = df_add(sx, g[5]);
+    sx = df_add(sx, -g[6]);
+    sx = df_add(sx, -g[7]);
+    sx = df_add(sx, g[8]);
+    sy = df_add(sy, -g[4]);
+    sy = df_add(sy, g[5]);
+    sy = df_add(sy, g[6]);
+    sy = df_add(sy, -g[7]);
+    sy = df_add(sy, -g[8]);
+    se = df_add(se, g[2]);
+    se = df_add(se, g[3]);
+    se = df_add(se, g[4]);
+#pragma unroll
+    for (int a = 5; a < 9; ++a) se = df_add(se, 2.0f * g[a]);
+    const double n = P.nsum_ref + df_value(sn);
+    const double jx = df_value(sx), jy = df_value(sy);
+    const double E = P.esum_ref + df_value(se);
+    double r = (double)__frcp_rn((float)n);  // 1/n: FP32 seed, two Newton steps
+    r = fma(r, fma(-n, r, 1.0), r);
+    r = fma(r, fma(-n, r, 1.0), r);
+    // the closure quantities in FP32 from the step's own deviation moments
+    // (delta = 3/2 - J_2 without cancellation), as the step decides them
+    const CellMom m = dev_moments(P, g);
+    float theta_f = 0.0f, mu_f = 0.0f, t_f = 0.0f;
+    double theta = 0.0, mu = 0.0, t = 0.0;
+    int cl = 0;
+    if (STAT == STAT_FD) {
+      const float J2 = 1.5f - m.delta;
+      cl = (J2 == J2 && (J2 >= Lf.j2_hi || J2 <= Lf.j2_lo)) ? 1 : 0;
+      float xf;
+      j4_from_delta_f(m.delta, Lf, &xf);
+      t_f = 1.0f / (fmaxf(xf, 0.0f) + log1pf(expf(-fabsf(xf))));  // t = T/T_F = 1/f_1(x)
+      theta_f = m.n * t_f * (float)(1.0 / (2.0 * kPi));            // theta = n t/(2 pi)
+      mu_f = theta_f * xf;
+      t = t_f; theta = theta_f; mu = mu_f;
+    } else if (STAT == STAT_FT) {
+      // fixed theta: t = 2 pi theta/n, x = a + ln(1 - e^{-a}) with a = 1/t
+      theta = P.theta;
+      t = 2.0 * kPi * theta * r;
+      const double a = n / (2.0 * kPi * theta);
+      mu = theta * (a + log(-expm1(-a)));
+    } else if (STAT == STAT_T0) {
+      theta = 0.0; t = 0.0; mu = n * (1.0 / (2.0 * kPi));
+    } else {
+      theta = mu = t = __longlong_as_double(0x7ff8000000000000LL);
+    }
+    if (on) on[i] = n;
+    if (oux) oux[i] = (jx + 0.5 * P.fx) * r;  // velocity at the time level under a body force
+    if (ouy) ouy[i] = (jy + 0.5 * P.fy) * r;
+    if (oT) oT[i] = theta;
+    if (omu) omu[i] = mu;
+    if (ot) ot[i] = t;
+    acc[0] = n; acc[1] = jx; acc[2] = jy; acc[3] = E;
+    acc[4] = cl;
+    bool fin = true;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) fin = fin && isfinite(g[a]);
+    acc[5] = (fin && isfinite(n)) ? 0.0 : 1.0;
+  }
+  // fixed-order block reduction, as moments_kernel
+  __shared__ double sh[kMomThreads / 32][kNPartial];
+#pragma unroll
+  for (int k = 0; k < kNPartial; ++k) {
+    double v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    acc[k] = v;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < kNPartial; ++k) sh[wid][k] = acc[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < kNPartial) {
+    double v = 0.0;
+#pragma unroll
+    for (int w = 0; w < kMomThreads / 32; ++w) v += sh[w][threadIdx.x];
+    partials[(int64_t)blockIdx.x * kNPartial + threadIdx.x] = v;
+  }
+}
+
 }  // namespace lbm

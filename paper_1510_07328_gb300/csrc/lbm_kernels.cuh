@@ -30,6 +30,7 @@ struct ProbDev {
   double n_ref, t_ref;               // deviation reference state (n_ref = 0: absolute storage)
   double j2_ref, ndelta_ref;         // J_2(t_ref), n_ref (3/2 - J_2(t_ref))
   double wref[9];                    // W_a^ref = w_a(J_2(t_ref)) n_ref
+  double nsum_ref, esum_ref;         // sum W^ref and sum W^ref |e|^2 (the deviations' offsets)
   double theta;                      // fixed-theta closure: theta = n_ref t_ref/(2 pi) of the problem
   struct {
     float omega, n_ref, ndelta_ref;
@@ -345,9 +346,9 @@ __global__ void set_pop_kernel(T* __restrict__ f, ProbDev P, int64_t plane, cons
 constexpr int kMomThreads = 256;
 constexpr int kNPartial = 6;  // sum n, jx, jy, E, clamped, nonfinite
 
-// F32CL (deviation-stored contexts): the closure quantities x, t, theta, mu
-// from the FP32 inversion of the step; n, u and the sums stay FP64.
-template <class T, int STAT, bool F32CL = false>
+// FP64 storage (deviation storage has moments_dev_kernel): n, u, the sums
+// and the FP64 inversion for x, t, theta, mu.
+template <class T, int STAT>
 __global__ void __launch_bounds__(kMomThreads) moments_kernel(const T* __restrict__ f, ProbDev P, int64_t plane,
                                                               InvLimits L, InvLimitsF Lf, double* __restrict__ on,
                                                               double* __restrict__ oux, double* __restrict__ ouy,
@@ -378,16 +379,8 @@ __global__ void __launch_bounds__(kMomThreads) moments_kernel(const T* __restric
     if (STAT == STAT_FD) {
       const double J2 = 1.5 * (E / n - (ux * ux + uy * uy));
       double xx;
-      if (F32CL) {
-        cl = (J2 >= L.j2_hi || J2 <= L.j2_lo) ? 1 : 0;
-        float xf;
-        j4_from_delta_f((float)(1.5 - J2), Lf, &xf);
-        xx = (double)xf;
-        t = (double)(1.0f / (fmaxf(xf, 0.0f) + log1pf(expf(-fabsf(xf)))));  // t = T/T_F = 1/f_1(x)
-      } else {
-        j4_fp64(J2, L, Lf, &xx, &cl);
-        t = 1.0 / (fmax(xx, 0.0) + log1p(exp(-fabs(xx))));  // t = T/T_F = 1/f_1(x)
-      }
+      j4_fp64(J2, L, Lf, &xx, &cl);
+      t = 1.0 / (fmax(xx, 0.0) + log1p(exp(-fabs(xx))));  // t = T/T_F = 1/f_1(x)
       theta = n * t / (2.0 * kPi);     // theta = n t/(2 pi), T_F = n/(2 pi)
       mu = theta * xx;
     } else if (STAT == STAT_FT) {
