@@ -121,16 +121,6 @@ __device__ __forceinline__ float j4_degenerate_f(float s) {
          rcp_a((3.0f * s + kPi2f) * (15.0f * s * s + 30.0f * kPi2f * s + 7.0f * kPi2f * kPi2f));
 }
 
-// J_4 with the first two series terms of f_2, f_3, f_4 (error O(y^3)).
-__device__ __forceinline__ float j4_tail_f(float x) {
-  const float y = expm_a(x);
-  float p2, p3, p4;
-  fd_poly_f(x, p2, p3, p4);
-  const float f2 = p2 - y * (1.0f - 0.25f * y);
-  const float f3 = p3 + y * (1.0f - 0.125f * y);
-  const float f4 = p4 - y * (1.0f - 0.0625f * y);
-  return f3 * f3 * rcp_a(f2 * f4);
-}
 
 // f_0..f_4 for x >= 4 (y = e^{-x} <= 0.019): three series terms in Horner
 // form (the fourth is below 2e-10 of f_2) and log1p(y) to y^4.
@@ -168,6 +158,34 @@ __device__ __forceinline__ float x_degenerate_fit(float delta) {
   return x;
 }
 
+// J_4 for x >= 17 straight from delta = 3/2 - J_2 (no root, no division): a
+// degree-4 polynomial in delta over [0, 1.02 delta(17)], within 1.6e-10 of
+// the degenerate closed form J_4 = P_3^2/(P_2 P_4) at the quadratic root
+// (whose dropped e^{-x} tails are below 3.4e-9 of J_4 there); about one
+// FP32 ulp in FP32 evaluation (least-squares fit, fit_x_of_j2.py).
+__device__ __forceinline__ float j4_degenerate_poly(float delta) {
+  constexpr float c[5] = {-6.607502108e+00f, -3.215488438e+00f, 1.066513921e+00f, -8.888885225e-01f,
+                          1.333333333e+00f};
+  float j = c[0];
+#pragma unroll
+  for (int k = 1; k < 5; ++k) j = fmaf(j, delta, c[k]);
+  return j;
+}
+
+// J_4 for 7 < x < 17 straight from delta: a degree-7 polynomial in
+// v = (delta - m)/h (v in [-1, 1] over [0.98 delta(17), 1.02 delta(7)]),
+// within 1.4e-9 of J_4 = f_3^2/(f_2 f_4) (least-squares fit to mpmath's
+// polylogarithm, fit_x_of_j2.py); about one FP32 ulp in FP32 evaluation.
+__device__ __forceinline__ float j4_mid_poly(float delta) {
+  constexpr float c[8] = {3.285286587e-07f, -6.328906060e-07f, -9.770357170e-07f, 1.359526894e-05f,
+                          -7.823930935e-05f, 6.168045261e-04f, -2.594511986e-02f, 1.292719233e+00f};
+  const float v = fmaf(delta, 3.121395636e+01f, -4.803407843e-02f * 3.121395636e+01f);
+  float j = c[0];
+#pragma unroll
+  for (int k = 1; k < 8; ++k) j = fmaf(j, v, c[k]);
+  return j;
+}
+
 // Starting value of the Newton branch (J_2(x_lo) < J_2 <= J_2(7)): x as a
 // degree-8 polynomial in v = ln((J_2 - 1)/(3/2 - J_2)), largest error 4.0e-5
 // over x in [x(t = 10) - 0.05, 7.3] (least-squares fit to J_2 = f_2^2/(f_1 f_3)
@@ -186,10 +204,11 @@ __device__ __forceinline__ float x_start_general(float J2) {
 // resolution; *xout receives x).
 //  * non-finite input: propagated at once;
 //  * J_2 beyond the clamp interval: x at the nearest end;
-//  * x >= 17 (delta <= 3/2 - J_2(17)): the degenerate quadratic root and the
-//    closed-form J_4;
+//  * x >= 17 (delta <= 3/2 - J_2(17)): x from the degenerate quadratic root,
+//    J_4 from its polynomial in delta (j4_degenerate_poly);
 //  * 7 < x < 17 (delta < 3/2 - J_2(7)): x from the fit x_degenerate_fit
-//    (FP32-exact), J_4 with the first two series terms (error O(e^{-3x}));
+//    (FP32-exact), J_4 from its polynomial in delta (j4_mid_poly); a caller
+//    that needs only J_4 (the step) computes no x in either branch;
 //  * otherwise safeguarded Newton on J_2(x) from the fitted start
 //    x_start_general (within 4e-5), each step one evaluation of f_0..f_4
 //    (three-term series for x >= 4), stopping when the step is below
@@ -212,15 +231,13 @@ __device__ __forceinline__ float j4_from_delta_f(float delta, const InvLimitsF& 
     *xout = L.x_lo;
     return f.f3 * f.f3 * rcp_a(f.f2 * f.f4);
   }
-  if (delta <= kDelta17) {
-    const float s = deg_root_f(delta);
-    *xout = sqrt_a(s);
-    return j4_degenerate_f(s);
+  if (delta <= kDelta17) {  // x (for callers that use it) from the degenerate root
+    *xout = sqrt_a(deg_root_f(delta));
+    return j4_degenerate_poly(delta);
   }
   if (delta < kDelta7) {
-    const float x = x_degenerate_fit(delta);
-    *xout = x;
-    return j4_tail_f(x);
+    *xout = x_degenerate_fit(delta);
+    return j4_mid_poly(delta);
   }
   float lo = L.x_lo, hi = 8.0f;  // J_2(8) > J_2(7): the root lies below
   float x = fminf(fmaxf(x_start_general(J2), lo), hi);

@@ -2,7 +2,10 @@
 generator (paper_1510_07328_gb300/fit_x_of_j2.py, mpmath only): the header's
 coefficients are the generator's; the Newton start stays within its stated
 4.0e-5 of x, and the degenerate-range fit within 1e-8 relative, on points the
-fits did not use; the branch thresholds are 3/2 - J_2(7) and 3/2 - J_2(17)."""
+fits did not use; the branch thresholds are 3/2 - J_2(7) and 3/2 - J_2(17).
+The two polynomials that give J_4 straight from delta = 3/2 - J_2 (x >= 17
+and 7 < x < 17) are the generator's and hold against the polylogarithm's
+J_4, in exact arithmetic and in the header's FP32 evaluation."""
 import os
 import re
 import sys
@@ -64,3 +67,67 @@ def test_degenerate_fit_matches_generator_and_holds():
     d = np.array([float(1.5 - gen.j2(x)) for x in xs])
     u = (np.log(d) - m) / h
     assert (np.abs(np.polyval(c_hdr, u) - xs) / xs).max() < 1e-8
+
+
+def header_j4_polys():
+    src = open(HEADER).read()
+    deg = re.search(r"j4_degenerate_poly\(float delta\) \{\s*constexpr float c\[5\] = \{([^}]*)\}", src).group(1)
+    mid = re.search(r"j4_mid_poly\(float delta\) \{\s*constexpr float c\[8\] = \{([^}]*)\}", src).group(1)
+    ih, m_ih, ih2 = re.search(r"fmaf\(delta, ([0-9.e+-]+)f, -([0-9.e+-]+)f \* ([0-9.e+-]+)f\)", src).groups()
+    assert ih == ih2
+    cd = np.array([float(v.strip().rstrip("f")) for v in deg.split(",")])
+    cm = np.array([float(v.strip().rstrip("f")) for v in mid.split(",")])
+    return cd, cm, float(m_ih), float(ih)
+
+
+def horner_fp32(c, v):
+    """The header's Horner evaluation in FP32, each step one rounding (fmaf)."""
+    c32 = np.asarray(c, dtype=np.float32).astype(np.float64)
+    v = np.asarray(v, dtype=np.float32).astype(np.float64)
+    y = np.full_like(v, c32[0])
+    for k in range(1, len(c32)):
+        y = (y * v + c32[k]).astype(np.float32).astype(np.float64)
+    return y
+
+
+def test_j4_polynomials_match_generator():
+    cd, cm, m_hdr, ih_hdr = header_j4_polys()
+    c_gen, err, _ = gen.fit_j4_degenerate()
+    np.testing.assert_allclose(cd, c_gen, rtol=1e-8, atol=1e-12)
+    assert err < 2e-10
+    c_gen, m, h, err = gen.fit_j4_mid()
+    np.testing.assert_allclose(cm, c_gen, rtol=1e-8, atol=1e-14)
+    assert abs(m_hdr - m) < 1e-10 and abs(ih_hdr - 1.0 / h) < 1e-6 and err < 2e-9
+
+
+def test_j4_polynomials_against_polylog_off_the_fit_points():
+    """J_4 from delta against J_4 = f_3^2/(f_2 f_4) of mpmath's polylogarithm
+    at points the fits did not use: x in [17, 300] for the degenerate
+    polynomial (its dropped tails are below 3.4e-9 there) and x in (7, 17)
+    for the middle one; exact arithmetic within 4e-9 and 2e-9, and the
+    header's FP32 evaluation within 2 FP32 ulps of J_4."""
+    cd, cm, m_ih, ih = header_j4_polys()
+    mp.mp.dps = 30
+    ulp = 2.0 ** -23
+    xs = np.concatenate([17.0 + 13.0 * (np.arange(23) + 0.37) / 23, 30.0 + 270.0 * (np.arange(11) + 0.5) / 11])
+    d = np.array([float(1.5 - gen.j2(x)) for x in xs])
+    J = np.array([float(gen.j4(x)) for x in xs])
+    assert (np.abs(np.polyval(cd, d) - J) / J).max() < 4e-9
+    assert (np.abs(horner_fp32(cd, d) - J) / J).max() < 2 * ulp
+    xs = 7.0 + 10.0 * (np.arange(31) + 0.43) / 31
+    d = np.array([float(1.5 - gen.j2(x)) for x in xs])
+    J = np.array([float(gen.j4(x)) for x in xs])
+    v = d * ih - m_ih * ih
+    assert (np.abs(np.polyval(cm, v) - J) / J).max() < 2e-9
+    v32 = (np.float32(d) * np.float32(ih)).astype(np.float64) - np.float32(np.float32(m_ih) * np.float32(ih))
+    assert (np.abs(horner_fp32(cm, v32) - J) / J).max() < 2 * ulp
+
+
+def test_j4_closed_form_is_the_degenerate_limit():
+    """The degenerate polynomial's target: 4/3 at delta = 0, and equal to the
+    polylogarithm's J_4 to the size of the dropped tails at x = 17 and 40."""
+    mp.mp.dps = 30
+    assert abs(float(gen.j4_closed_form(0.0)) - 4.0 / 3.0) < 1e-15
+    for x, tol in ((17.0, 4e-9), (40.0, 1e-15)):
+        d = 1.5 - gen.j2(x)
+        assert abs(float(gen.j4_closed_form(d) / gen.j4(x)) - 1.0) < tol
