@@ -35,6 +35,8 @@ static __global__ void setup_kernel(InvLimits* out) {
   L.x_hi = x_of_t(kTMin);
   L.j2_lo = j2_of(fd_eval(L.x_lo));
   L.j2_hi = j2_of(fd_eval(L.x_hi));
+  L.j4_lo = j4_of(fd_eval(L.x_lo));
+  L.j4_hi = j4_of(fd_eval(L.x_hi));
   *out = L;
 }
 
@@ -428,7 +430,8 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->ph.data(), ctx->pd, sizeof(ProbDev) * ctx->nprob, cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cleanup(LBM_ECUDA, std::string("lbm_create: setup: ") + cudaGetErrorString(e));
-  ctx->limf = InvLimitsF{(float)ctx->lim.x_lo, (float)ctx->lim.x_hi, (float)ctx->lim.j2_lo, (float)ctx->lim.j2_hi};
+  ctx->limf = InvLimitsF{(float)ctx->lim.x_lo,  (float)ctx->lim.x_hi,  (float)ctx->lim.j2_lo,
+                         (float)ctx->lim.j2_hi, (float)ctx->lim.j4_lo, (float)ctx->lim.j4_hi};
   e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cleanup(LBM_ECUDA, std::string("lbm_create: stream: ") + cudaGetErrorString(e));
   *out = ctx;

@@ -45,6 +45,7 @@ struct FD5 {
 struct InvLimits {
   double x_lo, x_hi;    // x(t_max), x(t_min)
   double j2_lo, j2_hi;  // J_2 at those x
+  double j4_lo, j4_hi;  // J_4 at those x
 };
 
 __device__ __forceinline__ void fd_poly(double x, double& p2, double& p3, double& p4) {

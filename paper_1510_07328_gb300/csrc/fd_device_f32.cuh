@@ -12,7 +12,7 @@ constexpr float kPi2f = 9.8696044010893586f;
 constexpr float kXDegF = 17.0f;  // e^-17 = 4e-8: S_n tails below FP32 resolution
 
 struct InvLimitsF {
-  float x_lo, x_hi, j2_lo, j2_hi;
+  float x_lo, x_hi, j2_lo, j2_hi, j4_lo, j4_hi;  // the clamp interval's ends: x, J_2 and J_4
 };
 
 struct FD5f {
@@ -186,6 +186,23 @@ __device__ __forceinline__ float j4_mid_poly(float delta) {
   return j;
 }
 
+// J_4 for x_lo < x <= 7 straight from delta: a degree-12 polynomial in
+// v = (delta - m)/h (v in [-1, 1] over [delta(7.1), delta(x_lo - 0.05)],
+// x_lo = x(t = 10)), within 5.6e-10 of J_4 = f_3^2/(f_2 f_4) (Chebyshev
+// least-squares fit to mpmath's polylogarithm, fit_x_of_j2.py); about one
+// FP32 ulp in FP32 evaluation.
+__device__ __forceinline__ float j4_low_poly(float delta) {
+  constexpr float c[13] = {3.751275144e-06f,  -8.171843462e-06f, 5.219605688e-06f,  -9.016432491e-06f,
+                           3.008137632e-05f,  -5.869911291e-05f, 1.010758946e-04f,  -1.385486611e-04f,
+                           3.636938822e-05f,  2.824311568e-04f,  1.345504631e-02f,  -1.320218322e-01f,
+                           1.124292938e+00f};
+  const float v = fmaf(delta, 4.861925282e+00f, -2.824715949e-01f * 4.861925282e+00f);
+  float j = c[0];
+#pragma unroll
+  for (int k = 1; k < 13; ++k) j = fmaf(j, v, c[k]);
+  return j;
+}
+
 // Starting value of the Newton branch (J_2(x_lo) < J_2 <= J_2(7)): x as a
 // degree-8 polynomial in v = ln((J_2 - 1)/(3/2 - J_2)), largest error 4.0e-5
 // over x in [x(t = 10) - 0.05, 7.3] (least-squares fit to J_2 = f_2^2/(f_1 f_3)
@@ -200,22 +217,43 @@ __device__ __forceinline__ float x_start_general(float J2) {
   return x;
 }
 
+// x for x_lo < x <= 7 from J_2 (J_2(x_lo) < J_2 <= J_2(7)): safeguarded
+// Newton on J_2(x) from the fitted start x_start_general (within 4e-5), each
+// step one evaluation of f_0..f_3 (three-term series for x >= 4), stopping
+// when the step is below 5e-4 |x| and returning x + dx (second-order
+// remainder below 1e-7 |x|): one evaluation in practice, at most 24.
+// J_2' = J_2 (2 f_1/f_2 - f_0/f_1 - f_2/f_3), from d f_n/dx = f_{n-1}.
+__device__ __forceinline__ float x_general_f(float J2, const InvLimitsF& L) {
+  float lo = L.x_lo, hi = 8.0f;  // J_2(8) > J_2(7): the root lies below
+  float x = fminf(fmaxf(x_start_general(J2), lo), hi);
+#pragma unroll 1
+  for (int it = 0; it < 24; ++it) {
+    const FD5f f = x >= 4.0f ? fd_eval_deg_f(x) : fd_eval_f(x);
+    const float i1 = rcp_a(f.f1), i2 = rcp_a(f.f2), i3 = rcp_a(f.f3);
+    const float j = f.f2 * f.f2 * i1 * i3;
+    const float g = j - J2;
+    const float dj = j * (2.0f * f.f1 * i2 - f.f0 * i1 - f.f2 * i3);
+    const float dx = -g * rcp_a(dj);
+    if (g < 0.0f) lo = x; else hi = x;
+    if (fabsf(dx) < 5e-4f * fabsf(x) || it == 23) return x + dx;
+    float xn = x + dx;
+    if (!(xn > lo && xn < hi)) xn = 0.5f * (lo + hi);
+    x = xn;
+  }
+  return x;
+}
+
 // J_4 from delta = 3/2 - J_2 in FP32 (the exact inversion, to FP32
 // resolution; *xout receives x).
 //  * non-finite input: propagated at once;
 //  * J_2 beyond the clamp interval: x at the nearest end;
-//  * x >= 17 (delta <= 3/2 - J_2(17)): x from the degenerate quadratic root,
-//    J_4 from its polynomial in delta (j4_degenerate_poly);
-//  * 7 < x < 17 (delta < 3/2 - J_2(7)): x from the fit x_degenerate_fit
-//    (FP32-exact), J_4 from its polynomial in delta (j4_mid_poly); a caller
-//    that needs only J_4 (the step) computes no x in either branch;
-//  * otherwise safeguarded Newton on J_2(x) from the fitted start
-//    x_start_general (within 4e-5), each step one evaluation of f_0..f_4
-//    (three-term series for x >= 4), stopping when the step is below
-//    5e-4 |x| and returning x + dx and J_4 + J_4' dx (second-order
-//    remainder < 1e-7): one evaluation in practice, at most 24.
-//    J_2' = J_2 (2 f_1/f_2 - f_0/f_1 - f_2/f_3), J_4' = J_4 (2 f_2/f_3 -
-//    f_1/f_2 - f_3/f_4), from d f_n/dx = f_{n-1}.
+//  * otherwise J_4 from its polynomial in delta on each of three intervals,
+//    and x (for callers that use it; the step does not) as follows:
+//    - x >= 17 (delta <= 3/2 - J_2(17)): j4_degenerate_poly, x from the
+//      degenerate quadratic root;
+//    - 7 < x < 17 (delta < 3/2 - J_2(7)): j4_mid_poly, x from the fit
+//      x_degenerate_fit (FP32-exact);
+//    - x_lo < x <= 7: j4_low_poly, x by x_general_f (Newton).
 __device__ __forceinline__ float j4_from_delta_f(float delta, const InvLimitsF& L, float* xout) {
   const float J2 = 1.5f - delta;
   if (!(J2 == J2)) {  // non-finite state: propagate without iterating
@@ -224,12 +262,11 @@ __device__ __forceinline__ float j4_from_delta_f(float delta, const InvLimitsF& 
   }
   if (!(J2 < L.j2_hi)) {
     *xout = L.x_hi;
-    return j4_degenerate_f(L.x_hi * L.x_hi);
+    return L.j4_hi;
   }
   if (J2 <= L.j2_lo) {
-    const FD5f f = fd_eval_f(L.x_lo);
     *xout = L.x_lo;
-    return f.f3 * f.f3 * rcp_a(f.f2 * f.f4);
+    return L.j4_lo;
   }
   if (delta <= kDelta17) {  // x (for callers that use it) from the degenerate root
     *xout = sqrt_a(deg_root_f(delta));
@@ -239,30 +276,8 @@ __device__ __forceinline__ float j4_from_delta_f(float delta, const InvLimitsF& 
     *xout = x_degenerate_fit(delta);
     return j4_mid_poly(delta);
   }
-  float lo = L.x_lo, hi = 8.0f;  // J_2(8) > J_2(7): the root lies below
-  float x = fminf(fmaxf(x_start_general(J2), lo), hi);
-  float J4 = 0.0f;
-#pragma unroll 1
-  for (int it = 0; it < 24; ++it) {
-    const FD5f f = x >= 4.0f ? fd_eval_deg_f(x) : fd_eval_f(x);
-    const float i1 = rcp_a(f.f1), i2 = rcp_a(f.f2), i3 = rcp_a(f.f3), i4 = rcp_a(f.f4);
-    const float j = f.f2 * f.f2 * i1 * i3;
-    const float g = j - J2;
-    const float dj = j * (2.0f * f.f1 * i2 - f.f0 * i1 - f.f2 * i3);
-    const float dx = -g * rcp_a(dj);
-    J4 = f.f3 * f.f3 * i2 * i4;
-    if (g < 0.0f) lo = x; else hi = x;
-    if (fabsf(dx) < 5e-4f * fabsf(x) || it == 23) {
-      const float dJ4 = J4 * (2.0f * f.f2 * i3 - f.f1 * i2 - f.f3 * i4);
-      *xout = x + dx;
-      return J4 + dJ4 * dx;
-    }
-    float xn = x + dx;
-    if (!(xn > lo && xn < hi)) xn = 0.5f * (lo + hi);
-    x = xn;
-  }
-  *xout = x;
-  return J4;
+  *xout = x_general_f(J2, L);
+  return j4_low_poly(delta);
 }
 
 // delta = 3/2 - J_2 and J_4 of the FD equilibrium at t = T/T_F, FP32.

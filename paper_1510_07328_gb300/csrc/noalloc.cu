@@ -141,6 +141,8 @@ __global__ void static_limits_kernel(InvLimits* out) {
   L.x_hi = x_of_t(kTMin);
   L.j2_lo = j2_of(fd_eval(L.x_lo));
   L.j2_hi = j2_of(fd_eval(L.x_hi));
+  L.j4_lo = j4_of(fd_eval(L.x_lo));
+  L.j4_hi = j4_of(fd_eval(L.x_hi));
   *out = L;
 }
 

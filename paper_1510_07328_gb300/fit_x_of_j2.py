@@ -19,7 +19,10 @@ needs J_4 and not x, skips x in both degenerate branches:
   [0, 1.02 delta(17)], fitted to the degenerate closed form (the e^{-x}
   tails it drops are below 3.4e-9 of J_4 there);
 - fit_j4_mid: 7 < x < 17, a degree-7 polynomial in (delta - m)/h over
-  [0.98 delta(17), 1.02 delta(7)], fitted to J_4 = f_3^2/(f_2 f_4).
+  [0.98 delta(17), 1.02 delta(7)], fitted to J_4 = f_3^2/(f_2 f_4);
+- fit_j4_low: x_lo < x <= 7, a degree-12 polynomial in (delta - m)/h over
+  [delta(7.1), delta(x_lo - 0.05)], fitted to J_4 = f_3^2/(f_2 f_4), in place
+  of the Newton iteration (which then runs only for callers that need x).
 
 Run: python paper_1510_07328_gb300/fit_x_of_j2.py  (prints the coefficients,
 highest degree first, and the largest errors of the fits).
@@ -83,6 +86,25 @@ def fit_j4_mid(deg: int = 7, samples: int = 700):
     return c, m, h, err
 
 
+def fit_j4_low(deg: int = 12, samples: int = 1500):
+    """J_4 for x_lo < x <= 7 (x_lo = x(t = 10)) as a polynomial in
+    v = (delta - m)/h, v in [-1, 1] over [delta(7.1), delta(x_lo - 0.05)]; a
+    Chebyshev least-squares fit over x in [x_lo - 0.05, 7.1], returned as
+    monomial coefficients of v.  Returns (coefficients, m, h, largest relative
+    error)."""
+    mp.mp.dps = 30
+    x_lo = float(mp.log(mp.e ** mp.mpf("0.1") - 1))
+    xs = np.linspace(x_lo - 0.05, 7.1, samples)
+    d = np.array([float(1.5 - j2(x)) for x in xs])
+    J = np.array([float(j4(x)) for x in xs])
+    lo, hi = float(1.5 - j2(7.1)), float(1.5 - j2(x_lo - 0.05))
+    m, h = 0.5 * (lo + hi), 0.5 * (hi - lo)
+    v = (d - m) / h
+    c = np.polynomial.chebyshev.cheb2poly(np.polynomial.chebyshev.chebfit(v, J, deg))[::-1]
+    err = float((np.abs(np.polyval(c, v) - J) / J).max())
+    return c, m, h, err
+
+
 def fit(deg: int = 8, samples: int = 800):
     mp.mp.dps = 30
     x_lo = float(mp.log(mp.e ** mp.mpf("0.1") - 1))  # t = 10: 1/f_1(x) = 10
@@ -126,4 +148,7 @@ if __name__ == "__main__":
     print(f"max relative error against the closed form {err:.2e}")
     c, m, h, err = fit_j4_mid()
     print("J_4 for 7 < x < 17, polynomial in (delta - m)/h:", ", ".join(f"{v:.9e}f" for v in c))
+    print(f"m = {m:.9e}, 1/h = {1.0 / h:.9e}, max relative error {err:.2e}")
+    c, m, h, err = fit_j4_low()
+    print("J_4 for x <= 7, polynomial in (delta - m)/h:", ", ".join(f"{v:.9e}f" for v in c))
     print(f"m = {m:.9e}, 1/h = {1.0 / h:.9e}, max relative error {err:.2e}")

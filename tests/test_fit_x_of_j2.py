@@ -3,9 +3,10 @@ generator (paper_1510_07328_gb300/fit_x_of_j2.py, mpmath only): the header's
 coefficients are the generator's; the Newton start stays within its stated
 4.0e-5 of x, and the degenerate-range fit within 1e-8 relative, on points the
 fits did not use; the branch thresholds are 3/2 - J_2(7) and 3/2 - J_2(17).
-The two polynomials that give J_4 straight from delta = 3/2 - J_2 (x >= 17
-and 7 < x < 17) are the generator's and hold against the polylogarithm's
-J_4, in exact arithmetic and in the header's FP32 evaluation."""
+The three polynomials that give J_4 straight from delta = 3/2 - J_2 (x >= 17,
+7 < x < 17 and x_lo < x <= 7) are the generator's and hold against the
+polylogarithm's J_4, in exact arithmetic and in the header's FP32
+evaluation."""
 import os
 import re
 import sys
@@ -80,6 +81,15 @@ def header_j4_polys():
     return cd, cm, float(m_ih), float(ih)
 
 
+def header_j4_low():
+    src = open(HEADER).read()
+    body = re.search(r"j4_low_poly\(float delta\) \{\s*constexpr float c\[13\] = \{([^}]*)\}", src).group(1)
+    ih, m_ih, ih2 = re.search(r"j4_low_poly.*?fmaf\(delta, ([0-9.e+-]+)f, -([0-9.e+-]+)f \* ([0-9.e+-]+)f\)", src,
+                              re.S).groups()
+    assert ih == ih2
+    return np.array([float(v.strip().rstrip("f")) for v in body.split(",")]), float(m_ih), float(ih)
+
+
 def horner_fp32(c, v):
     """The header's Horner evaluation in FP32, each step one rounding (fmaf)."""
     c32 = np.asarray(c, dtype=np.float32).astype(np.float64)
@@ -131,3 +141,23 @@ def test_j4_closed_form_is_the_degenerate_limit():
     for x, tol in ((17.0, 4e-9), (40.0, 1e-15)):
         d = 1.5 - gen.j2(x)
         assert abs(float(gen.j4_closed_form(d) / gen.j4(x)) - 1.0) < tol
+
+
+def test_j4_low_polynomial_matches_generator_and_holds():
+    """The polynomial that replaces the Newton iteration's J_4 for
+    x_lo < x <= 7 (x_lo = x(t = 10)): the generator's coefficients, and
+    within 1e-9 of the polylogarithm's J_4 off the fit points in exact
+    arithmetic, within 2 FP32 ulps in the header's FP32 evaluation."""
+    c_hdr, m_ih, ih = header_j4_low()
+    c_gen, m, h, err = gen.fit_j4_low()
+    np.testing.assert_allclose(c_hdr, c_gen, rtol=1e-8, atol=1e-15)
+    assert abs(m_ih - m) < 1e-10 and abs(ih - 1.0 / h) < 1e-6 and err < 1e-9
+    mp.mp.dps = 30
+    x_lo = float(mp.log(mp.e ** mp.mpf("0.1") - 1))
+    xs = x_lo + (7.0 - x_lo) * (np.arange(41) + 0.47) / 41
+    d = np.array([float(1.5 - gen.j2(x)) for x in xs])
+    J = np.array([float(gen.j4(x)) for x in xs])
+    v = d * ih - m_ih * ih
+    assert (np.abs(np.polyval(c_hdr, v) - J) / J).max() < 1e-9
+    v32 = (np.float32(d) * np.float32(ih)).astype(np.float64) - np.float32(np.float32(m_ih) * np.float32(ih))
+    assert (np.abs(horner_fp32(c_hdr, v32) - J) / J).max() < 2 * 2.0 ** -23
