@@ -52,6 +52,9 @@ CASES = {
     "random_300x5_bb": lambda: inputs.random_field(300, 5, 61, tau=0.7, bc_x="bounceback"),
     "random_129x9": lambda: inputs.random_field(129, 9, 62, tau=0.58, t_lo=0.005, t_hi=0.3),
     "riemann_400x4": lambda: inputs.riemann_1d(),
+    # hot states, x from about 3.3 down to the clamp end x(t = 10): the FP32
+    # inversion's low-x branch (J_4 from its polynomial in delta) over its range
+    "random_130x6_hot": lambda: inputs.random_field(130, 6, 63, tau=0.65, u_max=0.05, t_lo=0.3, t_hi=9.5),
 }
 
 
