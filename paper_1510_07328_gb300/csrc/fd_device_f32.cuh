@@ -1,7 +1,8 @@
 // FP32 Fermi-Dirac functions and the FP32 inversion J_2 -> (x, J_4) for
 // D = 2 (same expansions as fd_device.cuh, FP32 term counts, closed forms in
-// the degenerate regime).  Used by the reduced-precision step, and as the
-// starting value of the FP64 step's inversion.
+// the degenerate regime; J_4 straight from delta = 3/2 - J_2 by fitted
+// polynomials).  Used by the reduced-precision step, and as the starting
+// value of the FP64 step's inversion.
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
