@@ -250,16 +250,46 @@ KERNEL_SOURCES = {
 
 def kernel_family(kernel: str) -> str:
     """The KERNEL_SOURCES key of a kernel name: the learned-inversion engines
-    (stream_collide_surr_tc, _tc2, _mma) share one family."""
+    (stream_collide_surr_tc, _mma) share one family."""
     import re
 
     return re.sub(r"_(tc\d*|mma)$", "", kernel.split("<")[0])
 
 
+def strip_comments(src: str) -> str:
+    """C++ source without its comments (// to the end of the line, /* ... */),
+    string and character literals kept as written, trailing blanks and empty
+    lines dropped: what the compiler sees, so that editing a comment leaves a
+    kernel's source hash unchanged."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    lines = (line.rstrip() for line in "".join(out).splitlines())
+    return "\n".join(line for line in lines if line)
+
+
 def kernel_source_hash(kernel: str) -> str:
+    """Hash of the sources a kernel is built from, comments left out."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[kernel_family(kernel)]:
-        h.update(open(os.path.join(ROOT, "paper_1510_07328_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_1510_07328_gb300", "csrc", f), encoding="utf-8").read()
+        h.update(strip_comments(src).encode())
     return h.hexdigest()[:16]
 
 

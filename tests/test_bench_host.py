@@ -65,3 +65,14 @@ def test_workload_config_carries_the_contract_keys(workload):
     assert cfg["workload"].startswith(workload.split("_")[0])
     assert "L2" in cfg["l2"] and cfg["parallelism"] == "single GPU"
     assert bench.workload_config(a, 2, probs)["parallelism"] == "replicas x2"
+
+
+def test_source_hash_ignores_comments_only():
+    """The kernel source hash behind profiles/traffic.json sees what the
+    compiler sees: comments and blank lines do not change it, code does, and
+    comment markers inside string literals (inline PTX) are kept."""
+    base = 'asm("ld.global.f32 %0, [%1]; // not a comment");\nint a = 1;\n'
+    assert bench.strip_comments(base) == bench.strip_comments("/* header */\n" + base + "// trailing note\n\n")
+    assert bench.strip_comments(base) != bench.strip_comments(base.replace("a = 1", "a = 2"))
+    assert "// not a comment" in bench.strip_comments(base)
+    assert bench.strip_comments("x = y / z; /* a */ w = 1;") == "x = y / z;   w = 1;"
