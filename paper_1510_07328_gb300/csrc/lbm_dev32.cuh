@@ -206,11 +206,13 @@ __device__ __forceinline__ int gather_dev(const T* __restrict__ fin, int64_t pla
 // Tiles whose cells and neighbours are all inside the lattice (no wall, no
 // wrap) take the branch-free interior gather; edge tiles take the general one.
 // The next row's nine loads are issued before the current row's collision so
-// that each thread keeps two rows of loads in flight.
+// that each thread keeps two rows of loads in flight.  Eight CTAs per SM for
+// both storage types (9 and 10 measured no faster: the spills cost more than
+// the extra warps hide).
 template <class T, int STAT, int TY, bool PERSIST>
-__global__ void __launch_bounds__(kTileX, sizeof(T) == 4 ? 8 : 10) stream_collide_dev(const T* __restrict__ fin, T* __restrict__ fout,
-                                                                 const ProbDev* __restrict__ probs, int nprob,
-                                                                 int ntiles, int64_t plane, InvLimitsF L) {
+__global__ void __launch_bounds__(kTileX, 8) stream_collide_dev(const T* __restrict__ fin, T* __restrict__ fout,
+                                                                const ProbDev* __restrict__ probs, int nprob,
+                                                                int ntiles, int64_t plane, InvLimitsF L) {
   int tile = (int)blockIdx.x;
 #pragma unroll 1
   do {
