@@ -616,7 +616,10 @@ def run_ours(a, world, rank, local):
 
     value = world * cells * a.steps / (ms_max / 1e3) / 1e6
     per_launch_s = ms / 1e3 / a.steps
-    bytes_per_cell = (6 if a.workload == "d1v3" else 18) * BYTES_PER_ELEM[a.prec] + (1 if a.workload == "porous" else 0)
+    # the porous step also reads each cell's obstacle information: its 2-byte pull
+    # code with deviation storage, the 1-byte mask with FP64
+    bytes_per_cell = (6 if a.workload == "d1v3" else 18) * BYTES_PER_ELEM[a.prec] + (
+        (1 if a.prec == "f64" else 2) if a.workload == "porous" else 0)
     achieved = bytes_per_cell * cells / per_launch_s / 1e9
     peak, peak_kind = peaks()
     kname = {"f32": "stream_collide_dev<float,%s>", "bf16": "stream_collide_dev<bf16,%s>",

@@ -122,6 +122,7 @@ struct lbm_ctx {
   int64_t plane = 0, ntiles = 0;
   int dim = 2, q = 9;        // lattice: d2v9 or d1v3
   uint8_t* mask = nullptr;   // device: obstacle mask indexed like the cells (allocated on first use)
+  uint16_t* pcode = nullptr; // device: pull codes indexed like the cells (with the mask)
   bool porous = false;       // some problem has obstacles or a body force
   int rows = kTileYDefault;  // rows per tile
   int ctas = 0;              // 0: one CTA per tile; else a persistent grid of this many CTAs
@@ -938,15 +939,21 @@ lbm_status lbm_set_obstacles(lbm_ctx* ctx, int32_t problem, const uint8_t* solid
   ProbDev& P = ctx->ph[problem];
   if (!solid) {
     P.solid = nullptr;
+    P.pcode = nullptr;
     return upload_problems(ctx);
   }
   if (!ctx->mask) {
     CK(cudaMalloc(&ctx->mask, (size_t)ctx->plane));
     CK(cudaMemsetAsync(ctx->mask, 0, (size_t)ctx->plane, ctx->stream));
   }
+  if (!ctx->pcode) CK(cudaMalloc(&ctx->pcode, sizeof(uint16_t) * (size_t)ctx->plane));
   CK(cudaMemcpy2DAsync(ctx->mask + P.base, (size_t)P.pitch, solid, (size_t)P.nx, (size_t)P.nx, (size_t)P.ny,
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
   P.solid = ctx->mask;
+  P.pcode = ctx->pcode;
+  launch_pull_code(P, ctx->pcode, ctx->stream);  // from the mask just copied, in stream order
+  ++ctx->launches;
+  CKL();
   return upload_problems(ctx);
 }
 
@@ -981,6 +988,7 @@ lbm_status lbm_destroy(lbm_ctx* ctx) {
   if (ctx->wtc) cudaFree(ctx->wtc);
   if (ctx->wmm) cudaFree(ctx->wmm);
   if (ctx->mask) cudaFree(ctx->mask);
+  if (ctx->pcode) cudaFree(ctx->pcode);
   delete ctx->surr;
   delete ctx;
   return LBM_OK;

@@ -63,6 +63,8 @@ void launch_moments_d1(int prec, int stat, const void* f, const ProbDev& P, int6
 void launch_pop_d1(int prec, bool get, void* f, const ProbDev& P, int64_t plane, double* buf, cudaStream_t s);
 // d2v9 with obstacles (ProbDev::solid) and a body force (ProbDev::fx, fy)
 void launch_step_porous(int prec, int stat, int rows, unsigned grid, cudaStream_t s, const StepArgs& a);
+// Pull codes of one problem's cells from its obstacle mask (lbm_porous.cuh).
+void launch_pull_code(const ProbDev& P, uint16_t* code, cudaStream_t s);
 void launch_step_f64(int stat, int rows, unsigned grid, cudaStream_t s, const StepArgs& a);
 void launch_step_f32(int stat, int rows, unsigned grid, cudaStream_t s, const StepArgs& a);
 void launch_step_bf16(int stat, int rows, unsigned grid, cudaStream_t s, const StepArgs& a);

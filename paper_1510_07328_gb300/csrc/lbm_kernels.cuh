@@ -39,6 +39,7 @@ struct ProbDev {
     float two_pi_theta;  // 2 pi theta (fixed-theta closure)
   } f;              // FP32 copies for the reduced-precision step
   const uint8_t* solid;              // obstacle mask indexed like the cells (nonzero: solid), or null
+  const uint16_t* pcode;             // pull code of each cell (lbm_porous.cuh), set with solid, or null
   double fx, fy;                     // constant body force per cell and step
 };
 

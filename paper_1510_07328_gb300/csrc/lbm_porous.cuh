@@ -32,6 +32,51 @@ __device__ __forceinline__ void pull9_obst(const T* __restrict__ fin, int64_t pl
   v[8] = ld(8, q.rp, q.xm, 6);
 }
 
+// Pull code of one cell, for the FP32 / BF16 step with obstacles: bit a
+// (a = 1..8) is set when the pull source x - e_a of population a is solid or
+// beyond a wall, so that the population is the opposite one of the cell
+// itself (halfway bounce-back, the rule of pull9_obst); bit 0 when the cell
+// is solid.  Computed once per lbm_set_obstacles, 2 bytes per cell.
+__global__ void pull_code_kernel(ProbDev P, uint16_t* __restrict__ code) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)P.nx * P.ny) return;
+  const int y = (int)(i / P.nx), x = (int)(i % P.nx);
+  const PullIdx q = pull_index(P, x, y);
+  auto bad = [&](int64_t r, int xs) -> unsigned { return (r < 0 || xs < 0 || P.solid[r + xs] != 0) ? 1u : 0u; };
+  unsigned c = P.solid[q.row + x] != 0 ? 1u : 0u;
+  c |= bad(q.row, q.xm) << 1 | bad(q.rm, x) << 2 | bad(q.row, q.xp) << 3 | bad(q.rp, x) << 4;
+  c |= bad(q.rm, q.xm) << 5 | bad(q.rm, q.xp) << 6 | bad(q.rp, q.xp) << 7 | bad(q.rp, q.xm) << 8;
+  code[q.row + x] = (uint16_t)c;
+}
+
+// Pulled deviations of cell (x, y) through its pull code: every population's
+// address is chosen (neighbour or own opposite) before its single load, so
+// the pull has no branch and no mask scan.  `interior`: the row and its tile
+// have every neighbour on the lattice without wrapping (the offsets are then
+// constants); otherwise the wrapped offsets of pull_index32, whose
+// off-lattice entries are never used (their code bits are set).
+template <class T>
+__device__ __forceinline__ void gather_code(const T* __restrict__ fin, int64_t plane, const ProbDev& P, int x, int y,
+                                            bool interior, unsigned code, float g[9]) {
+  const int pt = P.pitch, off = (int)P.base + y * pt + x;
+  int s[9];
+  if (interior) {
+    s[1] = off - 1; s[2] = off - pt; s[3] = off + 1; s[4] = off + pt;
+    s[5] = off - pt - 1; s[6] = off - pt + 1; s[7] = off + pt + 1; s[8] = off + pt - 1;
+  } else {
+    const PullIdx32 q = pull_index32(P, x, y);
+    s[1] = q.row + q.xm; s[2] = q.rm + x; s[3] = q.row + q.xp; s[4] = q.rp + x;
+    s[5] = q.rm + q.xm; s[6] = q.rm + q.xp; s[7] = q.rp + q.xp; s[8] = q.rp + q.xm;
+  }
+  constexpr int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+  g[0] = Dev<T>::ld(fin[off]);
+#pragma unroll
+  for (int a = 1; a < 9; ++a) {
+    const int64_t idx = ((code >> a) & 1u) ? (int64_t)opp[a] * plane + off : (int64_t)a * plane + s[a];
+    g[a] = Dev<T>::ld(fin[idx]);
+  }
+}
+
 // FP64: BGK on f_eq(n, u) plus f_eq(n, u + F/n) - f_eq(n, u).
 template <int STAT>
 __device__ __forceinline__ void collide_force_f64(const ProbDev& P, const double f[9], double* __restrict__ fout,
@@ -151,10 +196,11 @@ __device__ __forceinline__ bool tile_clean(const ProbDev& P, int x0, int y0, int
 }
 
 // One CTA per tile of 128 cells x TY rows (PERSIST: a smaller grid walks the
-// tiles).  T = double: FP64 populations; float / bf16: deviations, with the
-// next row's loads issued before the current row's collision.  Tiles without
-// solid cells in reach take the pull without mask checks (for FP32 / BF16 the
-// branch-free interior gather).
+// tiles).  T = double: FP64 populations; tiles without solid cells in reach
+// take the pull without mask checks.  float / bf16: deviations, every cell
+// pulled through its pull code (gather_code; a problem without obstacles has
+// none and pulls plainly), with the next row's loads issued before the
+// current row's collision.
 template <class T, int STAT, int TY, bool PERSIST>
 __global__ void __launch_bounds__(kTileX, sizeof(T) == 8 ? 4 : (STAT == STAT_FD ? 6 : 8)) stream_collide_porous(const T* __restrict__ fin, T* __restrict__ fout,
                                                                 const ProbDev* __restrict__ probs, int nprob,
@@ -171,33 +217,21 @@ __global__ void __launch_bounds__(kTileX, sizeof(T) == 8 ? 4 : (STAT == STAT_FD 
     const int x = x0 + (int)threadIdx.x;
     const int y0 = ty * TY, y1 = min(y0 + TY, P.ny);
     const bool xin = x0 >= 1 && x0 + kTileX <= P.nx - 1;
-    // deviations: the first row's obstacle-free pull is issued before the
-    // mask scan, so that both latencies overlap; a tile with solid cells in
-    // reach pulls that row again with the checks (the first pull reads only
-    // cells of the lattice, solid ones included, and is discarded)
-    float gn[9];
     if constexpr (Stor<T>::dev) {
-      if (x < P.nx) gather_dev(fin, plane, P, x, y0, xin, gn);
-    }
-    const bool clean = tile_clean(P, x0, y0, y1);
-    if (x < P.nx) {
-      if constexpr (Stor<T>::dev) {
+      if (x < P.nx) {
         // pulled deviations of row y into g; false for a solid cell
         auto load = [&](int y, float g[9]) -> bool {
-          if (clean) {
+          if (P.pcode == nullptr) {  // no obstacles: the plain pull (walls included)
             gather_dev(fin, plane, P, x, y, xin, g);
             return true;
           }
-          if (is_solid(P, P.base + (int64_t)y * P.pitch + x)) return false;
-          T v[9];
-          pull9_obst(fin, plane, P, x, y, v);
-#pragma unroll
-          for (int a = 0; a < 9; ++a) g[a] = Dev<T>::ld(v[a]);
-          return true;
+          const unsigned code = P.pcode[(int)P.base + y * P.pitch + x];
+          gather_code(fin, plane, P, x, y, xin && y >= 1 && y <= P.ny - 2, code, g);
+          return (code & 1u) == 0u;
         };
         // the next row's loads are issued before the current row's collision
-        bool fn = true;
-        if (!clean) fn = load(y0, gn);
+        float gn[9];
+        bool fn = load(y0, gn);
 #pragma unroll 1
         for (int y = y0; y < y1; ++y) {
           float g[9];
@@ -218,7 +252,10 @@ __global__ void __launch_bounds__(kTileX, sizeof(T) == 8 ? 4 : (STAT == STAT_FD 
           }
           relax_force_store_dev<T, STAT>(P, g, m, J2, J4, fout, plane, (int)(P.base + (int64_t)y * P.pitch + x));
         }
-      } else {
+      }
+    } else {
+      const bool clean = tile_clean(P, x0, y0, y1);
+      if (x < P.nx) {
 #pragma unroll 1
         for (int y = y0; y < y1; ++y) {
           const int64_t c = P.base + (int64_t)y * P.pitch + x;

@@ -34,6 +34,11 @@ static void stat_t(int stat, int rows, unsigned grid, cudaStream_t s, const Step
   }
 }
 
+void launch_pull_code(const ProbDev& P, uint16_t* code, cudaStream_t s) {
+  const int64_t cells = (int64_t)P.nx * P.ny;
+  pull_code_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(P, code);
+}
+
 void launch_step_porous(int prec, int stat, int rows, unsigned grid, cudaStream_t s, const StepArgs& a) {
   switch (prec) {
     case 0: stat_t<double>(stat, rows, grid, s, a); break;
