@@ -220,7 +220,10 @@ lbm_status lbm_set_populations(lbm_ctx* ctx, int32_t problem, const double* f, i
  * is solid takes the opposite population of its own cell (halfway
  * bounce-back, as at the walls); solid cells are not updated and
  * lbm_moments reports them as n = u = T = mu = t = 0, outside the diag sums.
- * The first call allocates one byte per cell of the context.
+ * The call also builds each cell's 16-bit pull code (which of its nine pull
+ * sources are solid or beyond a wall, and whether it is solid itself), which
+ * the FP32 / BF16 step pulls through.  The first call allocates three bytes
+ * per cell of the context (mask and codes).
  *
  * lbm_set_force: force (fx, fy) per cell and step in lattice units, applied
  * by the exact difference method: after the BGK relaxation each fluid cell
