@@ -67,10 +67,20 @@ def test_step_parity_f64(L, stat, c):
     lat.close()
 
 
+# reduced storage pulls through the per-cell pull codes: periodic wraps, a
+# ragged last tile with bounce-back walls, and discs that touch both walls
+REDUCED_CASES = [(150, 40, 33, "periodic", None), (129, 33, 32, "bounceback", None),
+                 (129, 33, 34, "bounceback", [(1, 10), (127, 21), (64, 0)])]
+
+
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
 @pytest.mark.parametrize("stat", ["fd", "mb"])
-def test_step_parity_reduced(L, prec, stat):
-    p, solid, f = case(150, 40, 33, stat)
+@pytest.mark.parametrize("c", REDUCED_CASES, ids=["periodic", "bounceback", "discs_on_walls"])
+def test_step_parity_reduced(L, prec, stat, c):
+    nx, ny, seed, bc, centres = c
+    p, solid, f = case(nx, ny, seed, stat, bc, centres=centres, radius=2.5 if centres else 4)
+    if centres:  # the discs reach the walls at x = 0 and x = nx - 1, and wrap at y = 0
+        assert solid[:, 0].any() and solid[:, -1].any() and solid[0, :].any() and solid[-1, :].any()
     n_ref, t_ref = 0.95, 0.45
     from oracle import fd
 
