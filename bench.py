@@ -787,41 +787,54 @@ def extras(a, prob, dev_fields, lbm, torch, stream, value, net=None, local=0):
     lr.close()
     if a.inv == "exact" and a.prec in ("f32", "bf16"):
         res["surrogate"] = surrogate_extras(a, prob, dev_fields, lbm, torch, stream, value, v64, local)
-    # end to end through the public API with host buffers: H2D of the initial
-    # fields, K steps, D2H of the moments
-    # inputs and outputs in pinned host memory (filled before the timed region)
-    def pinned():
-        return torch.empty((prob.ny, prob.nx), dtype=torch.float64, pin_memory=True).numpy()
-
-    host = {}
-    for k in ("n", "ux", "uy", "t"):
-        host[k] = pinned()
-        host[k][...] = getattr(prob, k)
-    outs = {k: pinned() for k in ("n", "ux", "uy", "T")}
+    # end to end through the public API with host buffers: the initial fields
+    # host -> device, K steps, the moments device -> host; inputs and outputs
+    # in pinned host memory (filled before the timed region).  Reduced
+    # storage exchanges float arrays (lbm_init_fields_f32 / lbm_moments_f32,
+    # the calls a user of that storage makes); the double calls are measured
+    # beside them.
     le = lbm.Lattice([prob], stat="fd", prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05,
                      inv=a.inv, surrogate=net, engine=eng)
 
-    def cycle():
-        lbm.lbm_init_riemann(le.ctx, 0, "field", fields=host)  # host fields -> device inside the call
-        le.step(a.steps)
-        lbm.lbm_moments(le.ctx, 0, **outs)  # device -> host, synchronises
+    def e2e_cycles(f32):
+        dt = torch.float32 if f32 else torch.float64
+        host = {}
+        for k in ("n", "ux", "uy", "t"):
+            host[k] = torch.empty((prob.ny, prob.nx), dtype=dt, pin_memory=True).numpy()
+            host[k][...] = getattr(prob, k)
+        outs = {k: torch.empty((prob.ny, prob.nx), dtype=dt, pin_memory=True).numpy() for k in ("n", "ux", "uy", "T")}
 
-    cycle()  # untimed: the context's one-time staging allocations and step-graph capture
-    torch.cuda.synchronize()
-    els = []
-    for _ in range(5):
-        t0 = time.perf_counter()
-        cycle()
-        els.append(time.perf_counter() - t0)
+        def cycle():
+            if f32:
+                lbm.lbm_init_fields_f32(le.ctx, 0, host["n"], host["ux"], host["uy"], host["t"])
+                le.step(a.steps)
+                lbm.lbm_moments_f32(le.ctx, 0, **outs)  # device -> host, synchronises
+            else:
+                lbm.lbm_init_riemann(le.ctx, 0, "field", fields=host)  # host fields -> device inside the call
+                le.step(a.steps)
+                lbm.lbm_moments(le.ctx, 0, **outs)
+
+        cycle()  # untimed: the context's one-time staging allocations and step-graph capture
+        torch.cuda.synchronize()
+        els = []
+        for _ in range(5):
+            t0 = time.perf_counter()
+            cycle()
+            els.append(time.perf_counter() - t0)
+        el = statistics.median(els)
+        nbytes = 4 * cells * (4 if f32 else 8)
+        return {"value": cells * a.steps / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": nbytes / a.steps,
+                "d2h_bytes_per_step": nbytes / a.steps, "cycles_ms": [round(e * 1e3, 2) for e in els],
+                "fields": "float32" if f32 else "float64",
+                "note": "median of 5 timed cycles (init from pinned host fields + steps + moments to pinned "
+                        "host arrays, wall clock) after one untimed cycle"}
+
+    res["e2e_fp64_fields"] = e2e_cycles(False)
+    if a.prec in ("f32", "bf16"):
+        res["e2e"] = e2e_cycles(True)
+    else:
+        res["e2e"] = res.pop("e2e_fp64_fields")
     le.close()
-    el = statistics.median(els)
-    h2d = 4 * cells * 8
-    d2h = 4 * cells * 8
-    res["e2e"] = {"value": cells * a.steps / el / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": h2d / a.steps,
-                  "d2h_bytes_per_step": d2h / a.steps,
-                  "cycles_ms": [round(e * 1e3, 2) for e in els],
-                  "note": "median of 5 timed cycles (init from pinned host fields + steps + moments to pinned "
-                          "host arrays, wall clock) after one untimed cycle"}
     # CPU oracle on bounded samples: one core, then all host cores
     cb = oracle_sample_mlups(a.L, a.tau, a.cpu_seconds)
     res["cpu_baseline"] = {"value": cb["value"], "unit": "MLUPS", "cores": cb["cores"], "kind": "oracle",

@@ -203,6 +203,26 @@ typedef struct {
 lbm_status lbm_moments(lbm_ctx* ctx, int32_t problem, double* n, double* ux, double* uy,
                        double* T, double* mu, double* t, int32_t out_on_device, lbm_diag* diag);
 
+/* FP32 field exchange for contexts with FP32 or BF16 deviation storage on
+ * d2v9 (whose state carries FP32 precision): the FIELD initialisation and the
+ * moments with float arrays, half the bytes of the double calls over the host
+ * link.  The paper has no counterpart (an interface of this implementation).
+ *
+ * lbm_init_fields_f32: per-cell arrays n, ux, uy, t of nx*ny floats, host or
+ * device memory per on_device, with the meaning, checks and host-memory
+ * handling of FIELD in lbm_init_riemann; the result equals that of FIELD
+ * given the same values as doubles.
+ *
+ * lbm_moments_f32: as lbm_moments, into float arrays: each value is the
+ * double that lbm_moments reports, rounded once to float.  diag (FP64 sums)
+ * as lbm_moments.
+ *
+ * Errors: as the double calls; LBM_EUNSUPPORTED for FP64 storage or d1v3. */
+lbm_status lbm_init_fields_f32(lbm_ctx* ctx, int32_t problem, const float* n, const float* ux, const float* uy,
+                               const float* t, int32_t on_device);
+lbm_status lbm_moments_f32(lbm_ctx* ctx, int32_t problem, float* n, float* ux, float* uy, float* T, float* mu,
+                           float* t, int32_t out_on_device, lbm_diag* diag);
+
 /* Checkpoint / resume: copy the populations f_a (FP64, [Q][ny][nx]) of one
  * problem out of or into the library.  Storage of reduced precision converts
  * (f = W^ref + g on the way out, g = f - W^ref rounded on the way in).

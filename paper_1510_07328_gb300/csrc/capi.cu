@@ -10,6 +10,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "io_dev.cuh"
@@ -253,24 +254,24 @@ void launch_init_t(lbm_ctx* c, const ProbDev& P, const InitDesc& d) {
   }
 }
 
-template <class T, int STAT>
-void launch_moments_t(lbm_ctx* c, const ProbDev& P, double* o[6], unsigned g) {
+template <class T, int STAT, class O>
+void launch_moments_t(lbm_ctx* c, const ProbDev& P, O* o[6], unsigned g) {
   // deviation storage: error-free FP32 sums and the closure quantities from the FP32 inversion
   if constexpr (Stor<T>::dev)
-    moments_dev_kernel<T, STAT><<<g, kMomThreads, 0, c->stream>>>(
+    moments_dev_kernel<T, STAT, O><<<g, kMomThreads, 0, c->stream>>>(
         (const T*)c->buf[c->cur], P, c->plane, c->lim, c->limf, o[0], o[1], o[2], o[3], o[4], o[5], c->partials);
-  else
+  else if constexpr (std::is_same<O, double>::value)  // FP64 storage reports FP64 arrays only
     moments_kernel<T, STAT><<<g, kMomThreads, 0, c->stream>>>(
         (const T*)c->buf[c->cur], P, c->plane, c->lim, c->limf, o[0], o[1], o[2], o[3], o[4], o[5], c->partials);
 }
 
-template <class T>
-void launch_moments_p(lbm_ctx* c, const ProbDev& P, double* o[6], unsigned g) {
+template <class T, class O>
+void launch_moments_p(lbm_ctx* c, const ProbDev& P, O* o[6], unsigned g) {
   switch (c->stat) {
-    case LBM_STAT_FD: launch_moments_t<T, STAT_FD>(c, P, o, g); break;
-    case LBM_STAT_FD_T0: launch_moments_t<T, STAT_T0>(c, P, o, g); break;
-    case LBM_STAT_FT: launch_moments_t<T, STAT_FT>(c, P, o, g); break;
-    default: launch_moments_t<T, STAT_MB>(c, P, o, g); break;
+    case LBM_STAT_FD: launch_moments_t<T, STAT_FD, O>(c, P, o, g); break;
+    case LBM_STAT_FD_T0: launch_moments_t<T, STAT_T0, O>(c, P, o, g); break;
+    case LBM_STAT_FT: launch_moments_t<T, STAT_FT, O>(c, P, o, g); break;
+    default: launch_moments_t<T, STAT_MB, O>(c, P, o, g); break;
   }
 }
 
@@ -297,6 +298,84 @@ void* device_view(const void* p) {
     return nullptr;
   }
   return (a.type == cudaMemoryTypeHost && a.devicePointer != nullptr) ? a.devicePointer : nullptr;
+}
+
+// lbm_moments and lbm_moments_f32: O is the output arrays' type.
+template <class O>
+lbm_status moments_impl(lbm_ctx* ctx, int32_t problem, O* const user[6], int32_t out_on_device, lbm_diag* diag,
+                        const char* name) {
+  if (!ctx) return fail(nullptr, LBM_EINVAL, std::string(name) + ": NULL context");
+  if (problem < 0 || problem >= ctx->nprob) return fail(ctx, LBM_EINVAL, std::string(name) + ": bad problem index");
+  const ProbDev& P = ctx->ph[problem];
+  const int64_t cells = (int64_t)P.nx * P.ny;
+  const unsigned g = blocks_for(cells, kMomThreads);
+  if (ctx->partials_cap < (int64_t)g * kNPartial) {
+    if (ctx->partials) CK(cudaFree(ctx->partials));
+    ctx->partials = nullptr;
+    ctx->partials_cap = 0;
+    CK(cudaMalloc(&ctx->partials, sizeof(double) * kNPartial * g));
+    ctx->partials_cap = (int64_t)g * kNPartial;
+  }
+  O* o[6] = {user[0], user[1], user[2], user[3], user[4], user[5]};
+  bool staged[6] = {false, false, false, false, false, false};
+  if (!out_on_device) {
+    // page-locked host arrays are written in place by the kernel; the others
+    // through device staging and a copy
+    int nf = 0;
+    for (int a = 0; a < 6; ++a) {
+      if (!user[a]) continue;
+      void* v = device_view(user[a]);
+      if (v) {
+        o[a] = (O*)v;
+      } else {
+        staged[a] = true;
+        ++nf;
+      }
+    }
+    if (nf > 0) {
+      lbm_status s = ensure_tmp(ctx, nf * cells);  // doubles: room for nf arrays of O
+      if (s != LBM_OK) return s;
+    }
+    O* const tmp = reinterpret_cast<O*>(ctx->tmp);
+    int k = 0;
+    for (int a = 0; a < 6; ++a)
+      if (staged[a]) o[a] = tmp + (k++) * cells;
+  }
+  if (ctx->dim == 1) {
+    if constexpr (std::is_same<O, double>::value)
+      launch_moments_d1(ctx->prec, ctx->stat, ctx->buf[ctx->cur], P, ctx->plane, o, ctx->partials, g, ctx->stream);
+  } else {
+    switch (ctx->prec) {
+      case LBM_F64: launch_moments_p<double, O>(ctx, P, o, g); break;
+      case LBM_F32_DEV: launch_moments_p<float, O>(ctx, P, o, g); break;
+      default: launch_moments_p<__nv_bfloat16, O>(ctx, P, o, g); break;
+    }
+  }
+  CKL();
+  ctx->launches += 1;
+  if (diag) {
+    reduce_partials_kernel<<<1, 256, 0, ctx->stream>>>(ctx->partials, g, ctx->diag_d);
+    CKL();
+    ctx->launches += 1;
+  }
+  if (!out_on_device) {
+    for (int a = 0; a < 6; ++a)
+      if (staged[a]) CK(cudaMemcpyAsync(user[a], o[a], sizeof(O) * cells, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  if (diag) {
+    double h[kNPartial];
+    CK(cudaMemcpyAsync(h, ctx->diag_d, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    diag->sum_n = h[0];
+    diag->sum_jx = h[1];
+    diag->sum_jy = h[2];
+    diag->sum_E = h[3];
+    diag->clamped = (int64_t)h[4];
+    diag->nonfinite = (int64_t)h[5];
+  } else if (!out_on_device) {
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return LBM_OK;
 }
 
 }  // namespace
@@ -508,6 +587,52 @@ lbm_status lbm_init_riemann(lbm_ctx* ctx, int32_t problem, const lbm_riemann_des
   CKL();
   ctx->launches += 1;
   if (d->kind == LBM_INIT_FIELD && !d->field_on_device) CK(cudaStreamSynchronize(ctx->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_init_fields_f32(lbm_ctx* ctx, int32_t problem, const float* n, const float* ux, const float* uy,
+                               const float* t, int32_t on_device) {
+  if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_init_fields_f32: NULL context");
+  if (problem < 0 || problem >= ctx->nprob) return fail(ctx, LBM_EINVAL, "lbm_init_fields_f32: bad problem index");
+  if (ctx->dim != 2 || ctx->prec == LBM_F64)
+    return fail(ctx, LBM_EUNSUPPORTED, "lbm_init_fields_f32: needs d2v9 with FP32 or BF16 deviation storage");
+  if (!n || !ux || !uy || !t) return fail(ctx, LBM_EINVAL, "lbm_init_fields_f32: NULL field array");
+  const ProbDev& P = ctx->ph[problem];
+  const int64_t cells = (int64_t)P.nx * P.ny;
+  InitDesc k{};
+  k.kind = 3;  // FIELD, float arrays
+  if (on_device) {
+    k.nf = n;
+    k.uxf = ux;
+    k.uyf = uy;
+    k.tf = t;
+  } else {
+    const float* src[4] = {n, ux, uy, t};
+    void* view[4];
+    bool direct = true;
+    for (int a = 0; a < 4; ++a) direct = (view[a] = device_view(src[a])) != nullptr && direct;
+    if (direct) {  // page-locked host fields: the kernel reads them in place
+      k.nf = (const float*)view[0];
+      k.uxf = (const float*)view[1];
+      k.uyf = (const float*)view[2];
+      k.tf = (const float*)view[3];
+    } else {
+      lbm_status s = ensure_tmp(ctx, 2 * cells);  // doubles: room for four float arrays
+      if (s != LBM_OK) return s;
+      float* const tmp = reinterpret_cast<float*>(ctx->tmp);
+      for (int a = 0; a < 4; ++a)
+        CK(cudaMemcpyAsync(tmp + a * cells, src[a], sizeof(float) * cells, cudaMemcpyHostToDevice, ctx->stream));
+      k.nf = tmp;
+      k.uxf = tmp + cells;
+      k.uyf = tmp + 2 * cells;
+      k.tf = tmp + 3 * cells;
+    }
+  }
+  if (ctx->prec == LBM_F32_DEV) launch_init_t<float>(ctx, P, k);
+  else launch_init_t<__nv_bfloat16>(ctx, P, k);
+  CKL();
+  ctx->launches += 1;
+  if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
   return LBM_OK;
 }
 
@@ -783,77 +908,16 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int32_t steps_per_candidate, lbm_tiling* c
 
 lbm_status lbm_moments(lbm_ctx* ctx, int32_t problem, double* n, double* ux, double* uy, double* T, double* mu,
                        double* t, int32_t out_on_device, lbm_diag* diag) {
-  if (!ctx) return fail(nullptr, LBM_EINVAL, "lbm_moments: NULL context");
-  if (problem < 0 || problem >= ctx->nprob) return fail(ctx, LBM_EINVAL, "lbm_moments: bad problem index");
-  const ProbDev& P = ctx->ph[problem];
-  const int64_t cells = (int64_t)P.nx * P.ny;
-  const unsigned g = blocks_for(cells, kMomThreads);
-  if (ctx->partials_cap < (int64_t)g * kNPartial) {
-    if (ctx->partials) CK(cudaFree(ctx->partials));
-    ctx->partials = nullptr;
-    ctx->partials_cap = 0;
-    CK(cudaMalloc(&ctx->partials, sizeof(double) * kNPartial * g));
-    ctx->partials_cap = (int64_t)g * kNPartial;
-  }
-  double* user[6] = {n, ux, uy, T, mu, t};
-  double* o[6] = {n, ux, uy, T, mu, t};
-  bool staged[6] = {false, false, false, false, false, false};
-  if (!out_on_device) {
-    // page-locked host arrays are written in place by the kernel; the others
-    // through device staging and a copy
-    int nf = 0;
-    for (int a = 0; a < 6; ++a) {
-      if (!user[a]) continue;
-      void* v = device_view(user[a]);
-      if (v) {
-        o[a] = (double*)v;
-      } else {
-        staged[a] = true;
-        ++nf;
-      }
-    }
-    if (nf > 0) {
-      lbm_status s = ensure_tmp(ctx, nf * cells);
-      if (s != LBM_OK) return s;
-    }
-    int k = 0;
-    for (int a = 0; a < 6; ++a)
-      if (staged[a]) o[a] = ctx->tmp + (k++) * cells;
-  }
-  if (ctx->dim == 1) {
-    launch_moments_d1(ctx->prec, ctx->stat, ctx->buf[ctx->cur], P, ctx->plane, o, ctx->partials, g, ctx->stream);
-  } else {
-    switch (ctx->prec) {
-      case LBM_F64: launch_moments_p<double>(ctx, P, o, g); break;
-      case LBM_F32_DEV: launch_moments_p<float>(ctx, P, o, g); break;
-      default: launch_moments_p<__nv_bfloat16>(ctx, P, o, g); break;
-    }
-  }
-  CKL();
-  ctx->launches += 1;
-  if (diag) {
-    reduce_partials_kernel<<<1, 256, 0, ctx->stream>>>(ctx->partials, g, ctx->diag_d);
-    CKL();
-    ctx->launches += 1;
-  }
-  if (!out_on_device) {
-    for (int a = 0; a < 6; ++a)
-      if (staged[a]) CK(cudaMemcpyAsync(user[a], o[a], sizeof(double) * cells, cudaMemcpyDeviceToHost, ctx->stream));
-  }
-  if (diag) {
-    double h[kNPartial];
-    CK(cudaMemcpyAsync(h, ctx->diag_d, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    diag->sum_n = h[0];
-    diag->sum_jx = h[1];
-    diag->sum_jy = h[2];
-    diag->sum_E = h[3];
-    diag->clamped = (int64_t)h[4];
-    diag->nonfinite = (int64_t)h[5];
-  } else if (!out_on_device) {
-    CK(cudaStreamSynchronize(ctx->stream));
-  }
-  return LBM_OK;
+  double* const user[6] = {n, ux, uy, T, mu, t};
+  return moments_impl<double>(ctx, problem, user, out_on_device, diag, "lbm_moments");
+}
+
+lbm_status lbm_moments_f32(lbm_ctx* ctx, int32_t problem, float* n, float* ux, float* uy, float* T, float* mu,
+                           float* t, int32_t out_on_device, lbm_diag* diag) {
+  if (ctx && (ctx->dim != 2 || ctx->prec == LBM_F64))
+    return fail(ctx, LBM_EUNSUPPORTED, "lbm_moments_f32: needs d2v9 with FP32 or BF16 deviation storage");
+  float* const user[6] = {n, ux, uy, T, mu, t};
+  return moments_impl<float>(ctx, problem, user, out_on_device, diag, "lbm_moments_f32");
 }
 
 lbm_status lbm_get_populations(lbm_ctx* ctx, int32_t problem, double* f, int32_t on_device) {

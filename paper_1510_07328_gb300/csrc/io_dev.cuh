@@ -20,6 +20,8 @@ __global__ void init_dev_kernel(T* __restrict__ f, ProbDev P, int64_t plane, Ini
   double n, ux, uy, t;
   if (d.kind == 2) {
     n = d.n[i]; ux = d.ux[i]; uy = d.uy[i]; t = d.t[i];
+  } else if (d.kind == 3) {
+    n = d.nf[i]; ux = d.uxf[i]; uy = d.uyf[i]; t = d.tf[i];
   } else {
     const int r = d.kind == 0 ? (x >= d.x0) : (x >= d.x0) + 2 * (y >= d.y0);
     n = d.s[r][0]; ux = d.s[r][1]; uy = d.s[r][2]; t = d.s[r][3];

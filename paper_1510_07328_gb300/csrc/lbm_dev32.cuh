@@ -273,24 +273,26 @@ __device__ __forceinline__ double df_value(DFsum a) { return (double)a.hi + (dou
 // of 1e-16 relative.  n_ref = sum W_ref and E_ref = sum W_ref |e|^2 are the
 // reference weights' sums (ProbDev::nsum_ref, esum_ref).  The clamp count and
 // x, t, theta, mu come from the step's FP32 deviation moments and inversion.
-template <class T, int STAT>
+// O: the output arrays' type (double, or float for lbm_moments_f32: the same
+// values rounded once); the partial sums stay FP64.
+template <class T, int STAT, class O = double>
 __global__ void __launch_bounds__(kMomThreads) moments_dev_kernel(const T* __restrict__ f, ProbDev P, int64_t plane,
-                                                                  InvLimits L, InvLimitsF Lf, double* __restrict__ on,
-                                                                  double* __restrict__ oux, double* __restrict__ ouy,
-                                                                  double* __restrict__ oT, double* __restrict__ omu,
-                                                                  double* __restrict__ ot,
+                                                                  InvLimits L, InvLimitsF Lf, O* __restrict__ on,
+                                                                  O* __restrict__ oux, O* __restrict__ ouy,
+                                                                  O* __restrict__ oT, O* __restrict__ omu,
+                                                                  O* __restrict__ ot,
                                                                   double* __restrict__ partials) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t cells = (int64_t)P.nx * P.ny;
   double acc[kNPartial] = {0, 0, 0, 0, 0, 0};
   const int64_t c = i < cells ? P.base + (int64_t)(i / P.nx) * P.pitch + (int)(i % P.nx) : 0;
   if (i < cells && P.solid != nullptr && P.solid[c] != 0) {  // obstacle: no fluid
-    if (on) on[i] = 0.0;
-    if (oux) oux[i] = 0.0;
-    if (ouy) ouy[i] = 0.0;
-    if (oT) oT[i] = 0.0;
-    if (omu) omu[i] = 0.0;
-    if (ot) ot[i] = 0.0;
+    if (on) on[i] = (O)0;
+    if (oux) oux[i] = (O)0;
+    if (ouy) ouy[i] = (O)0;
+    if (oT) oT[i] = (O)0;
+    if (omu) omu[i] = (O)0;
+    if (ot) ot[i] = (O)0;
   } else if (i < cells) {
     float g[9];
 #pragma unroll
@@ -345,12 +347,12 @@ __global__ void __launch_bounds__(kMomThreads) moments_dev_kernel(const T* __res
     } else {
       theta = mu = t = __longlong_as_double(0x7ff8000000000000LL);
     }
-    if (on) on[i] = n;
-    if (oux) oux[i] = (jx + 0.5 * P.fx) * r;  // velocity at the time level under a body force
-    if (ouy) ouy[i] = (jy + 0.5 * P.fy) * r;
-    if (oT) oT[i] = theta;
-    if (omu) omu[i] = mu;
-    if (ot) ot[i] = t;
+    if (on) on[i] = (O)n;
+    if (oux) oux[i] = (O)((jx + 0.5 * P.fx) * r);  // velocity at the time level under a body force
+    if (ouy) ouy[i] = (O)((jy + 0.5 * P.fy) * r);
+    if (oT) oT[i] = (O)theta;
+    if (omu) omu[i] = (O)mu;
+    if (ot) ot[i] = (O)t;
     acc[0] = n; acc[1] = jx; acc[2] = jy; acc[3] = E;
     acc[4] = cl;
     bool fin = true;

@@ -291,9 +291,10 @@ struct Stor<__nv_bfloat16> {
 // ------------------------------------------------------------------ init
 
 struct InitDesc {
-  int32_t kind, x0, y0;
+  int32_t kind, x0, y0;  // kind 0 HALF, 1 QUADRANT, 2 FIELD (double arrays), 3 FIELD (float arrays)
   double s[4][4];  // n, ux, uy, t of up to four regions
   const double *n, *ux, *uy, *t;  // device arrays for FIELD
+  const float *nf, *uxf, *uyf, *tf;  // device arrays for FIELD with float values (deviation storage only)
 };
 
 template <class T, int STAT>

@@ -81,6 +81,8 @@ def _load():
         "lbm_init_riemann": (C.c_int, [V, C.c_int32, C.POINTER(lbm_riemann_desc)]),
         "lbm_step": (C.c_int, [V, C.c_int32]),
         "lbm_moments": (C.c_int, [V, C.c_int32, V, V, V, V, V, V, C.c_int32, C.POINTER(lbm_diag)]),
+        "lbm_init_fields_f32": (C.c_int, [V, C.c_int32, V, V, V, V, C.c_int32]),
+        "lbm_moments_f32": (C.c_int, [V, C.c_int32, V, V, V, V, V, V, C.c_int32, C.POINTER(lbm_diag)]),
         "lbm_get_populations": (C.c_int, [V, C.c_int32, V, C.c_int32]),
         "lbm_set_populations": (C.c_int, [V, C.c_int32, V, C.c_int32]),
         "lbm_destroy": (C.c_int, [V]),
@@ -115,8 +117,7 @@ EXPORTS = ("lbm_create", "lbm_init_riemann", "lbm_step", "lbm_moments", "lbm_get
            "lbm_conservation_sums_static", "lbm_set_tiling", "lbm_get_tiling", "lbm_autotune",
            "lbm_surrogate_targets", "lbm_surrogate_loss_grad", "lbm_surrogate_train", "lbm_surrogate_eval",
            "lbm_surrogate_load", "lbm_surrogate_stats", "lbm_surrogate_engine", "lbm_surrogate_wait_limit",
-           "lbm_set_obstacles",
-           "lbm_set_force")
+           "lbm_set_obstacles", "lbm_set_force", "lbm_init_fields_f32", "lbm_moments_f32")
 LBM_SURROGATE_FP32_PIPE, LBM_SURROGATE_TENSOR_CORES, LBM_SURROGATE_WARP_MMA = 0, 1, 2
 NPARAM = 4482
 
@@ -132,17 +133,18 @@ def _check(status: int, ctx) -> None:
         raise LbmError(status, LIB.lbm_last_error(ctx).decode())
 
 
-def _ptr(a) -> int | None:
-    """Address of a NumPy array or torch tensor (None stays NULL)."""
+def _ptr(a, dtype: str = "float64") -> int | None:
+    """Address of a NumPy array or torch tensor of the given element type
+    (None stays NULL)."""
     if a is None:
         return None
     if isinstance(a, np.ndarray):
-        if not a.flags["C_CONTIGUOUS"] or a.dtype != np.float64:
-            raise ValueError("host arrays must be C-contiguous float64")
+        if not a.flags["C_CONTIGUOUS"] or a.dtype != np.dtype(dtype):
+            raise ValueError(f"host arrays must be C-contiguous {dtype}")
         return a.ctypes.data
     if hasattr(a, "data_ptr"):
-        if not a.is_contiguous() or str(a.dtype) != "torch.float64":
-            raise ValueError("device tensors must be contiguous float64")
+        if not a.is_contiguous() or str(a.dtype) != f"torch.{dtype}":
+            raise ValueError(f"tensors must be contiguous {dtype}")
         return a.data_ptr()
     raise TypeError("expected a numpy array or a torch tensor")
 
@@ -193,6 +195,13 @@ def lbm_init_riemann(ctx, problem: int, kind: str, states=(), split=(0, 0), fiel
     _check(LIB.lbm_init_riemann(ctx, int(problem), C.byref(d)), ctx)
 
 
+def lbm_init_fields_f32(ctx, problem: int, n, ux, uy, t, on_device=False):
+    """FIELD initialisation from float32 arrays (FP32 / BF16 deviation storage)."""
+    keep = [np.ascontiguousarray(a, dtype=np.float32) if isinstance(a, np.ndarray) else a for a in (n, ux, uy, t)]
+    _check(LIB.lbm_init_fields_f32(ctx, int(problem), *[_ptr(a, "float32") for a in keep], 1 if on_device else 0),
+           ctx)
+
+
 def lbm_step(ctx, nsteps: int):
     _check(LIB.lbm_step(ctx, int(nsteps)), ctx)
 
@@ -202,6 +211,18 @@ def lbm_moments(ctx, problem: int, n=None, ux=None, uy=None, T=None, mu=None, t=
     dg = lbm_diag() if diag else None
     _check(LIB.lbm_moments(ctx, int(problem), _ptr(n), _ptr(ux), _ptr(uy), _ptr(T), _ptr(mu), _ptr(t),
                            1 if on_device else 0, C.byref(dg) if dg is not None else None), ctx)
+    if dg is not None:
+        return {"sum_n": dg.sum_n, "sum_jx": dg.sum_jx, "sum_jy": dg.sum_jy, "sum_E": dg.sum_E,
+                "clamped": dg.clamped, "nonfinite": dg.nonfinite}
+    return None
+
+
+def lbm_moments_f32(ctx, problem: int, n=None, ux=None, uy=None, T=None, mu=None, t=None, on_device=False,
+                    diag=False):
+    """lbm_moments into float32 arrays (FP32 / BF16 deviation storage)."""
+    dg = lbm_diag() if diag else None
+    _check(LIB.lbm_moments_f32(ctx, int(problem), *[_ptr(a, "float32") for a in (n, ux, uy, T, mu, t)],
+                               1 if on_device else 0, C.byref(dg) if dg is not None else None), ctx)
     if dg is not None:
         return {"sum_n": dg.sum_n, "sum_jx": dg.sum_jx, "sum_jy": dg.sum_jy, "sum_E": dg.sum_E,
                 "clamped": dg.clamped, "nonfinite": dg.nonfinite}
