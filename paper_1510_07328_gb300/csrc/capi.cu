@@ -308,7 +308,8 @@ lbm_status moments_impl(lbm_ctx* ctx, int32_t problem, O* const user[6], int32_t
   if (problem < 0 || problem >= ctx->nprob) return fail(ctx, LBM_EINVAL, std::string(name) + ": bad problem index");
   const ProbDev& P = ctx->ph[problem];
   const int64_t cells = (int64_t)P.nx * P.ny;
-  const unsigned g = blocks_for(cells, kMomThreads);
+  const bool dev = ctx->dim == 2 && ctx->prec != LBM_F64;  // moments_dev_kernel: kMomDevCells per thread
+  const unsigned g = blocks_for(cells, kMomThreads * (dev ? kMomDevCells : 1));
   if (ctx->partials_cap < (int64_t)g * kNPartial) {
     if (ctx->partials) CK(cudaFree(ctx->partials));
     ctx->partials = nullptr;

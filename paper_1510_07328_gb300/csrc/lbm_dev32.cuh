@@ -274,7 +274,9 @@ __device__ __forceinline__ double df_value(DFsum a) { return (double)a.hi + (dou
 // reference weights' sums (ProbDev::nsum_ref, esum_ref).  The clamp count and
 // x, t, theta, mu come from the step's FP32 deviation moments and inversion.
 // O: the output arrays' type (double, or float for lbm_moments_f32: the same
-// values rounded once); the partial sums stay FP64.
+// values rounded once); the partial sums stay FP64.  Each thread takes
+// kMomDevCells cells and each block writes one partial per sum (grid:
+// cells / (kMomThreads kMomDevCells) blocks).
 template <class T, int STAT, class O = double>
 __global__ void __launch_bounds__(kMomThreads) moments_dev_kernel(const T* __restrict__ f, ProbDev P, int64_t plane,
                                                                   InvLimits L, InvLimitsF Lf, O* __restrict__ on,
@@ -282,9 +284,13 @@ __global__ void __launch_bounds__(kMomThreads) moments_dev_kernel(const T* __res
                                                                   O* __restrict__ oT, O* __restrict__ omu,
                                                                   O* __restrict__ ot,
                                                                   double* __restrict__ partials) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t cells = (int64_t)P.nx * P.ny;
   double acc[kNPartial] = {0, 0, 0, 0, 0, 0};
+  // kMomDevCells cells per thread, strided by the block size (coalesced), so
+  // that the FP64 block reduction below is shared by several cells
+#pragma unroll 1
+  for (int kk = 0; kk < kMomDevCells; ++kk) {
+  const int64_t i = ((int64_t)blockIdx.x * kMomDevCells + kk) * blockDim.x + threadIdx.x;
   const int64_t c = i < cells ? P.base + (int64_t)(i / P.nx) * P.pitch + (int)(i % P.nx) : 0;
   if (i < cells && P.solid != nullptr && P.solid[c] != 0) {  // obstacle: no fluid
     if (on) on[i] = (O)0;
@@ -353,12 +359,13 @@ __global__ void __launch_bounds__(kMomThreads) moments_dev_kernel(const T* __res
     if (oT) oT[i] = (O)theta;
     if (omu) omu[i] = (O)mu;
     if (ot) ot[i] = (O)t;
-    acc[0] = n; acc[1] = jx; acc[2] = jy; acc[3] = E;
-    acc[4] = cl;
+    acc[0] += n; acc[1] += jx; acc[2] += jy; acc[3] += E;
+    acc[4] += cl;
     bool fin = true;
 #pragma unroll
     for (int a = 0; a < 9; ++a) fin = fin && isfinite(g[a]);
-    acc[5] = (fin && isfinite(n)) ? 0.0 : 1.0;
+    acc[5] += (fin && isfinite(n)) ? 0.0 : 1.0;
+  }
   }
   // fixed-order block reduction, as moments_kernel
   __shared__ double sh[kMomThreads / 32][kNPartial];

@@ -347,6 +347,7 @@ __global__ void set_pop_kernel(T* __restrict__ f, ProbDev P, int64_t plane, cons
 
 constexpr int kMomThreads = 256;
 constexpr int kNPartial = 6;  // sum n, jx, jy, E, clamped, nonfinite
+constexpr int kMomDevCells = 4;  // cells per thread of moments_dev_kernel
 
 // FP64 storage (deviation storage has moments_dev_kernel): n, u, the sums
 // and the FP64 inversion for x, t, theta, mu.
