@@ -143,3 +143,76 @@ def test_batched_256_sampled_autotuned(L):
             # |g| = |f - W_ref| <= |f| + |W_ref| <= 2 max|f| for these states
             assert np.abs(g - ref).max() <= tol_for("f32", fmax, 2 * fmax), (i, cx, cy)
     lat.close()
+
+
+def test_smooth_t_4096_sampled_learned(L):
+    """The learned step (network on tcgen05, polish, check, fallback) on the
+    4096^2 lattice in the launch configuration bench.py times (persistent
+    grid, network trained as there), against the exact FP64 oracle."""
+    import torch
+
+    n_tr, t_tr = inputs.surrogate_set(1_000_000, seed=4)
+    net, _ = L.lbm_surrogate_train(inputs.surrogate_init(11), n_tr, t_tr, epochs=32, batch=1024)
+    prob = inputs.smooth_t(4096, tau=0.8)
+    dev = {k: torch.from_numpy(getattr(prob, k)).cuda() for k in ("n", "ux", "uy", "t")}
+    lat = L.Lattice([prob], stat="fd", prec="f32", n_ref=0.9, t_ref=0.05, inv="surrogate", surrogate=net,
+                    engine="tensor")
+    lat.init(fields_on_device=dev)
+    lat.step(K)
+    st = L.lbm_surrogate_stats(lat.ctx)
+    cells = sample_cells(prob.nx, prob.ny, 48, seed=104)
+    got = gpu_cells(L, lat, 0, prob, cells)
+    lat.close()
+    del dev
+    assert st["evaluations"] > 0.9 * K * prob.nx * prob.ny and st["fallbacks"] <= 0.01 * st["evaluations"], st
+
+    def field(gy, gx):
+        return prob.n[gy, gx], prob.ux[gy, gx], prob.uy[gy, gx], prob.t[gy, gx]
+
+    for (cx, cy), g in zip(cells, got):
+        ref = window_oracle(field, prob.nx, prob.ny, prob.bc_x, prob.bc_y, prob.tau, cx, cy, K)
+        fmax = np.abs(ref).max()
+        assert np.abs(g - ref).max() <= tol_for("f32", fmax, fmax), (cx, cy)
+
+
+def test_porous_4096_sampled_autotuned(L):
+    """The porous step on the bench's 4096^2 disc lattice (4793 discs of
+    radius 3, MB closure, force (1e-6, 0), FP32 pull codes, autotuned
+    tiling), from random velocities so that the bounce-back on the discs
+    shows; sampled cells include ones next to the discs.  The oracle window
+    carries the same piece of the obstacle mask."""
+    import bench
+    import torch
+    from oracle import porous
+
+    nL, k, force = 4096, K, (1e-6, 0.0)
+    centres = inputs.disc_centres(nL, nL, bench.porous_discs(nL), 3, 13)
+    solid = inputs.disc_mask(nL, nL, centres, 3)
+    r = inputs.uniform(105, 2 * nL * nL)
+    ux = (0.05 * (2 * r[:nL * nL] - 1)).reshape(nL, nL)
+    uy = (0.05 * (2 * r[nL * nL:] - 1)).reshape(nL, nL)
+    prob = inputs.Problem(nL, nL, 0.7, "periodic", "periodic", np.ones((nL, nL)), ux, uy, np.full((nL, nL), 0.5),
+                          name="porous_4096", kind="field")
+    dev = {key: torch.from_numpy(getattr(prob, key)).cuda() for key in ("n", "ux", "uy", "t")}
+    lat = L.Lattice([prob], stat="mb", prec="f32", n_ref=1.0, t_ref=0.5)  # as bench.py
+    lat.set_obstacles(solid)
+    lat.set_force(*force)
+    lat.init(fields_on_device=dev)
+    L.lbm_autotune(lat.ctx, 2)
+    lat.init(fields_on_device=dev)
+    lat.step(k)
+    cells = sample_cells(nL, nL, 24, seed=106)
+    cells += [((cx + dx) % nL, (cy + dy) % nL) for cx, cy in centres[:12] for dx, dy in ((4, 0), (-3, 2), (0, -4))]
+    got = gpu_cells(L, lat, 0, prob, cells)
+    lat.close()
+    del dev
+    for (cx, cy), g in zip(cells, got):
+        wx = np.arange(cx - k, cx + k + 1) % nL
+        wy = np.arange(cy - k, cy + k + 1) % nL
+        gx, gy = np.meshgrid(wx, wy)
+        f = olbm.init_equilibrium(prob.n[gy, gx], ux[gy, gx], uy[gy, gx], prob.t[gy, gx], "mb")
+        ref = porous.run(f, solid[gy, gx], prob.tau, "mb", force, k)[:, k, k]
+        fmax = np.abs(ref).max()
+        assert np.abs(g - ref).max() <= tol_for("f32", fmax, fmax), (cx, cy)
+    # the near-disc cells do see a solid neighbour
+    assert any(solid[(cy + dy) % nL, (cx + dx) % nL] for cx, cy in cells[24:] for dx in (-1, 0, 1) for dy in (-1, 0, 1))
