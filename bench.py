@@ -42,8 +42,8 @@ BYTES_PER_ELEM = {"f64": 8, "f32": 4, "bf16": 2}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=25)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--reps", type=int, default=0, help="timed windows (0: enough for ~1 s, at most 60)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="f32", choices=["f32", "bf16", "f64"])
@@ -54,7 +54,7 @@ def parse():
                          "porous: the paper's porous sample (porosity 0.992, discs of radius 3) scaled to L x L")
     ap.add_argument("--cells1d", type=int, default=1 << 25, help="lattice length of the d1v3 workload")
     ap.add_argument("--autotune", action="store_true", help="autotune the tiling before timing (always on for batched and porous)")
-    ap.add_argument("--inv", default="exact", choices=["exact", "surrogate"],
+    ap.add_argument("--inv", default="exact", choices=["exact", "surrogate", "exact_f64"],
                     help="per-cell FD inversion: exact, or the learned network (trained first, on 1e6 pairs)")
     ap.add_argument("--train-epochs", type=int, default=32)
     ap.add_argument("--engine", default="tensor", choices=["tensor", "mma", "fp32"],
@@ -132,6 +132,7 @@ def workload_config(a, world, probs=None, tiling=None):
                     "mb": "d2v9 K=3 LBGK, Maxwell-Boltzmann limit (J = 1)"}[a.stat],
         "storage": {"f32": "FP32 deviations g = f - W_ref", "bf16": "BF16 deviations", "f64": "FP64 f"}[a.prec],
         "inversion": "exact (closed-form degenerate root for x >= 17, fitted x(delta) for 7 < x < 17, one Newton step from a fitted start below)" if a.inv == "exact"
+        else "exact in FP64 (Newton from the FP32 start, J_4 rounded once to FP32)" if a.inv == "exact_f64"
         else "learned network 2-64-64-2 (%s) + one third-order polish + residual check, exact fallback"
         % {"tensor": "tcgen05 MMAs over 128-cell tile rows", "mma": "warp-level MMAs, activations in registers",
            "fp32": "FP32 pipe"}[a.engine],
@@ -239,6 +240,7 @@ def max_over_ranks(world, v: float) -> float:
 _EXACT_SRC = ("lbm_kernels.cuh", "fd_device.cuh", "fd_device_f32.cuh", "lbm_dev32.cuh", "launch.h")
 KERNEL_SOURCES = {
     "stream_collide_dev": _EXACT_SRC + ("step_f32.cu", "step_bf16.cu"),
+    "stream_collide_dev_x64": _EXACT_SRC + ("lbm_dev_x64.cuh", "step_x64.cu"),
     "stream_collide_f64": ("lbm_kernels.cuh", "fd_device.cuh", "fd_device_f32.cuh", "launch.h", "step_f64.cu"),
     "stream_collide_surr": _EXACT_SRC + ("surrogate.cuh", "tc_sm100.cuh", "lbm_surr.cuh", "lbm_surr_mma.cuh",
                                          "step_surr.cu"),
@@ -314,9 +316,10 @@ def profiled_traffic(kernel: str, workload: str, cells: int):
 def _oracle_window_worker(job):
     """One host core: advance one oracle window for about job["seconds"] of
     stepping (or exactly job["steps"] timed steps), re-initialised from its
-    initial state every job["window_steps"] steps as the GPU arm is, so that no
-    non-finite state is ever timed.  The W warm-up steps of every window are
-    untimed.  Returns (cell updates timed, seconds timed, steps timed)."""
+    initial state every job["window_steps"] timed steps, as the GPU arm's
+    windows are.  The W warm-up steps of every window are
+    untimed.  Returns (cell updates timed, seconds timed, steps timed,
+    windows whose state was non-finite when they ended)."""
     import numpy as _np
 
     f0 = job["f0"]
@@ -324,6 +327,7 @@ def _oracle_window_worker(job):
     cells = int(_np.prod(f0.shape[1:]))
     timed = 0.0
     steps = 0
+    bad = 0
     with _np.errstate(invalid="ignore", divide="ignore", over="ignore"):
         while True:
             f = f0
@@ -335,7 +339,8 @@ def _oracle_window_worker(job):
                 timed += time.perf_counter() - t0
                 steps += 1
                 if (job.get("steps") and steps >= job["steps"]) or (not job.get("steps") and timed >= job["seconds"]):
-                    return cells * steps, timed, steps
+                    return cells * steps, timed, steps, bad + int(not _np.isfinite(f).all())
+            bad += int(not _np.isfinite(f).all())
 
 
 def _oracle_step(job):
@@ -380,10 +385,20 @@ def oracle_pool_mlups(jobs, processes: int):
     return updates / secs / 1e6, res
 
 
+# Timed steps after which an oracle window restarts from its initial state.
+# The energy closure is linearly unstable at the smooth-t workload's states
+# (t down to 0.01): its windows first turn non-finite at step 24 to 28 (with
+# walls at the window's x ends; 17 to 40 with a periodic wrap, whose second,
+# nearby density step speeds it up), so 5 warm-up steps plus at most 16
+# timed ones keep every timed oracle state finite.
+ORACLE_WINDOW_STEPS = 16
+
+
 def smooth_t_windows(L: int, tau: float, count: int, window: int = 48, stat: str = "fd"):
     """count initial oracle states: window x window pieces of the smooth-t
-    lattice straddling the density step at x = L/2, at different rows
-    (periodic wrap in place of the rest of the lattice)."""
+    lattice straddling the density step at x = L/2, at different rows (walls
+    at the window's x ends and a periodic wrap in y in place of the rest of
+    the lattice: one density step per window, as around x = L/2)."""
     from oracle import lbm as olbm
     from paper_1510_07328_gb300 import inputs
 
@@ -400,20 +415,25 @@ def smooth_t_windows(L: int, tau: float, count: int, window: int = 48, stat: str
     return out
 
 
-def oracle_sample_mlups(L: int, tau: float, seconds: float, window: int = 48):
+def oracle_sample_mlups(L: int, tau: float, seconds: float, window: int = 48, warmup: int = 5, steps: int = 20):
     """The CPU oracle on windows of the smooth-t workload: one core alone, then
     every host core at once (independent windows, one per core).  Each window
-    restarts from its initial state every 25 steps after 3 warm-up steps, the
-    regime of the GPU arm's timed windows."""
+    restarts from its initial state every `steps` timed steps after `warmup`
+    warm-up steps, the regime of the GPU arm's timed windows."""
     cores = host_cores()
     f0s = smooth_t_windows(L, tau, cores, window)
-    one = [{"f0": f0s[0], "tau": tau, "warmup": 3, "window_steps": 25, "seconds": seconds * 0.4}]
+    steps = min(steps, ORACLE_WINDOW_STEPS)
+    one = [{"f0": f0s[0], "tau": tau, "warmup": warmup, "window_steps": steps, "seconds": seconds * 0.4,
+            "bc_x": "bounceback"}]
     v1, r1 = oracle_pool_mlups(one, 1)
-    jobs = [{"f0": f, "tau": tau, "warmup": 3, "window_steps": 25, "seconds": seconds * 0.6} for f in f0s]
+    jobs = [{"f0": f, "tau": tau, "warmup": warmup, "window_steps": steps, "seconds": seconds * 0.6,
+             "bc_x": "bounceback"} for f in f0s]
     vall, rall = oracle_pool_mlups(jobs, cores)
     return {"value": vall, "cores": cores, "value_1core": v1,
-            "sample": f"{window}x{window} windows of the lattice at x = L/2 (periodic wrap), one per core; each "
-                      f"restarts from its initial state every 25 timed steps after 3 warm-up steps; "
+            "nonfinite_windows": sum(r[3] for r in rall) + r1[0][3],
+            "sample": f"{window}x{window} windows of the lattice at x = L/2 (walls at the window's x ends, periodic "
+                      f"in y), one per core; each "
+                      f"restarts from its initial state every {steps} timed steps after {warmup} warm-up steps; "
                       f"{sum(r[2] for r in rall)} timed steps over {cores} cores in {max(r[1] for r in rall):.1f} s; "
                       f"1 core alone: {r1[0][2]} steps in {r1[0][1]:.1f} s"}
 
@@ -424,7 +444,7 @@ def oracle_jobs(a, count: int):
     of the lattice."""
     from paper_1510_07328_gb300 import inputs
 
-    base = {"warmup": a.warmup, "window_steps": 25, "steps": a.steps}
+    base = {"warmup": a.warmup, "window_steps": a.steps, "steps": a.steps}
     if a.workload == "d1v3":
         from oracle import lbm1d
 
@@ -457,8 +477,10 @@ def oracle_jobs(a, count: int):
             jobs.append(dict(base, f0=f, kind="d2v9", tau=p.tau, stat=a.stat))
         return jobs, "32 columns around the density step of batched problem k (one problem per core)"
     f0s = smooth_t_windows(a.L, a.tau, count, 32, a.stat)
-    jobs = [dict(base, f0=f, kind="d2v9", tau=a.tau, stat=a.stat) for f in f0s]
-    return jobs, "32x32 windows of the lattice at x = L/2, at different rows, one per core"
+    jobs = [dict(base, f0=f, kind="d2v9", tau=a.tau, stat=a.stat, bc_x="bounceback",
+                 window_steps=min(a.steps, ORACLE_WINDOW_STEPS)) for f in f0s]
+    return jobs, ("32x32 windows of the lattice at x = L/2 (walls at the window's x ends), at different rows, "
+                  f"one per core, restarting every {min(a.steps, ORACLE_WINDOW_STEPS)} timed steps")
 
 
 def run_reference(a, world, rank):
@@ -467,12 +489,12 @@ def run_reference(a, world, rank):
     cores = host_cores()
     jobs, what = oracle_jobs(a, cores)
     # every core advances its own window: W untimed warm-up steps from the
-    # initial state, then the K timed steps, restarting every 25 steps (the
-    # GPU arm's regime: no non-finite state is timed)
+    # initial state, then the K timed steps, restarting after them (the GPU
+    # arm's regime of timed windows)
     mlups, res = oracle_pool_mlups(jobs, cores)
     el = max(r[1] for r in res)
     cfg = workload_config(a, 1, inputs_for_config(a))
-    sample = f"{what}: {a.steps} timed steps each after {a.warmup} warm-up steps, restarting every 25 steps"
+    sample = f"{what}: {a.steps} timed steps each after {a.warmup} warm-up steps"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": 0,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": el / a.steps * 1e3, "higher_is_better": True,
@@ -624,6 +646,8 @@ def run_ours(a, world, rank, local):
     peak, peak_kind = peaks()
     kname = {"f32": "stream_collide_dev<float,%s>", "bf16": "stream_collide_dev<bf16,%s>",
              "f64": "stream_collide_f64<%s>"}[a.prec] % a.stat.upper()
+    if a.inv == "exact_f64" and a.prec != "f64":
+        kname = "stream_collide_dev_x64<%s>" % {"f32": "float", "bf16": "bf16"}[a.prec]
     if a.inv == "surrogate":
         kname = {"tensor": "stream_collide_surr_tc<%s>", "mma": "stream_collide_surr_mma<%s>",
                  "fp32": "stream_collide_surr<%s>"}[a.engine] % {"f32": "float", "bf16": "bf16"}[a.prec]
@@ -757,6 +781,35 @@ def surrogate_extras(a, prob, dev_fields, lbm, torch, stream, value, v64, local)
     return out
 
 
+def x64_extras(a, prob, dev_fields, lbm, torch, stream, value, errs_f32inv):
+    """The same storage with the Fermi-Dirac inversion in FP64
+    (inv="exact_f64"): its rate over 10 steps after the warm-up, and its field
+    errors against the plain FP64 path beside those of the FP32 inversion, so
+    that the share of the T error that the inversion's precision causes is
+    read off directly."""
+    k = 10
+    lat = lbm.Lattice([prob], stat="fd", prec=a.prec, stream=stream.cuda_stream, n_ref=0.9, t_ref=0.05,
+                      inv="exact_f64")
+    with torch.cuda.stream(stream):
+        lat.init(fields_on_device=dev_fields)
+        lat.step(a.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    errs = field_errors_vs_fp64(lbm, torch, stream, prob, dev_fields, lat)
+    lat.close()
+    keys = ("steps", "T_max_rel", "T_rms_rel", "n_max_rel", "u_max_abs")
+    return {"value": prob.cells * k / (ms / 1e3) / 1e6, "unit": "MLUPS", "steps": k,
+            "kernel": "stream_collide_dev_x64<%s>" % {"f32": "float", "bf16": "bf16"}[a.prec],
+            "ratio_to_fp32_inversion": prob.cells * k / (ms / 1e3) / 1e6 / value,
+            "field_error_vs_fp64": [{q: e[q] for q in keys} for e in errs],
+            "field_error_vs_fp64_fp32_inversion": [{q: e[q] for q in keys} for e in errs_f32inv]}
+
+
 def extras(a, prob, dev_fields, lbm, torch, stream, value, net=None, local=0):
     """FP64 comparison on the same lattice, the learned inversion (when the
     headline is the exact one), end-to-end timing through host buffers, and
@@ -786,6 +839,7 @@ def extras(a, prob, dev_fields, lbm, torch, stream, value, net=None, local=0):
     res["field_error_vs_fp64"] = field_errors_vs_fp64(lbm, torch, stream, prob, dev_fields, lr)
     lr.close()
     if a.inv == "exact" and a.prec in ("f32", "bf16"):
+        res["fp64_inversion"] = x64_extras(a, prob, dev_fields, lbm, torch, stream, value, res["field_error_vs_fp64"])
         res["surrogate"] = surrogate_extras(a, prob, dev_fields, lbm, torch, stream, value, v64, local)
     # end to end through the public API with host buffers: the initial fields
     # host -> device, K steps, the moments device -> host; inputs and outputs
@@ -836,9 +890,10 @@ def extras(a, prob, dev_fields, lbm, torch, stream, value, net=None, local=0):
         res["e2e"] = res.pop("e2e_fp64_fields")
     le.close()
     # CPU oracle on bounded samples: one core, then all host cores
-    cb = oracle_sample_mlups(a.L, a.tau, a.cpu_seconds)
+    cb = oracle_sample_mlups(a.L, a.tau, a.cpu_seconds, warmup=a.warmup, steps=a.steps)
     res["cpu_baseline"] = {"value": cb["value"], "unit": "MLUPS", "cores": cb["cores"], "kind": "oracle",
-                           "value_1core": cb["value_1core"], "sample": cb["sample"]}
+                           "value_1core": cb["value_1core"], "nonfinite_windows": cb["nonfinite_windows"],
+                           "sample": cb["sample"]}
     return res
 
 

@@ -76,7 +76,18 @@ typedef enum { LBM_STAT_FD = 0, LBM_STAT_FD_T0 = 1, LBM_STAT_MB = 2, LBM_STAT_FT
  * diag sums stay FP64 sums of the stored values). */
 typedef enum { LBM_F64 = 0, LBM_F32_DEV = 1, LBM_BF16_DEV = 2 } lbm_prec;
 
-typedef enum { LBM_INV_EXACT = 0, LBM_INV_SURROGATE = 1 } lbm_inv;
+/* The Fermi-Dirac inversion J_2 -> (x, J_4) of Sect. "Generalized polynomials
+ * in D dimensions" (J_2 = f_2^2/(f_1 f_3) solved for x, J_4 = f_3^2/(f_2 f_4)).
+ * EXACT: in the storage's arithmetic (FP64 Newton for LBM_F64; FP32 fits in
+ * delta = 3/2 - J_2 for deviation storage).  SURROGATE: the learned inversion
+ * (lbm_surrogate_*).  EXACT_F64: deviation storage (FP32 or BF16) whose step
+ * keeps FP32 populations, sums and equilibrium but inverts in FP64: delta from
+ * the FP32 deviation moments, x by FP64 Newton to 1e-13, J_4 rounded once to
+ * FP32; the initial closure J_2(t), J_4(t) and the T, mu, t that lbm_moments
+ * reports come from the same FP64 functions.  LBM_STAT_FD on d2v9 only (else
+ * LBM_EUNSUPPORTED); with LBM_F64 it is the same as EXACT.  No obstacles or
+ * forces. */
+typedef enum { LBM_INV_EXACT = 0, LBM_INV_SURROGATE = 1, LBM_INV_EXACT_F64 = 2 } lbm_inv;
 
 typedef enum { LBM_BC_PERIODIC = 0, LBM_BC_BOUNCEBACK = 1 } lbm_bc;
 

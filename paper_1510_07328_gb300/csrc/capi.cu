@@ -16,6 +16,7 @@
 #include "io_dev.cuh"
 #include "launch.h"
 #include "lbm.h"
+#include "lbm_dev_x64.cuh"
 #include "lbm_kernels.cuh"
 #include "surrogate.cuh"
 
@@ -207,6 +208,10 @@ void launch_step(lbm_ctx* c, const void* in, void* out, cudaStream_t s) {
     }
     return;
   }
+  if (c->inv == LBM_INV_EXACT_F64 && c->prec != LBM_F64) {  // deviation storage, FP64 inversion
+    launch_step_x64(c->prec, c->rows, grid, s, a);
+    return;
+  }
   switch (c->prec) {
     case LBM_F64: launch_step_f64(c->stat, c->rows, grid, s, a); break;
     case LBM_F32_DEV: launch_step_f32(c->stat, c->rows, grid, s, a); break;
@@ -238,6 +243,10 @@ void launch_init_t(lbm_ctx* c, const ProbDev& P, const InitDesc& d) {
   const unsigned g = blocks_for(cells, 256);
   // deviation storage: the FP32 equilibrium of the reduced-precision step
   if constexpr (Stor<T>::dev) {
+    if (c->inv == LBM_INV_EXACT_F64) {  // FD statistics: the closure from t in FP64
+      init_dev_kernel<T, STAT_FD, true><<<g, 256, 0, c->stream>>>(f, P, c->plane, d);
+      return;
+    }
     switch (c->stat) {
       case LBM_STAT_FD: init_dev_kernel<T, STAT_FD><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
       case LBM_STAT_FD_T0: init_dev_kernel<T, STAT_T0><<<g, 256, 0, c->stream>>>(f, P, c->plane, d); break;
@@ -273,6 +282,19 @@ void launch_moments_p(lbm_ctx* c, const ProbDev& P, O* o[6], unsigned g) {
     case LBM_STAT_FT: launch_moments_t<T, STAT_FT, O>(c, P, o, g); break;
     default: launch_moments_t<T, STAT_MB, O>(c, P, o, g); break;
   }
+}
+
+// T, mu, t of deviation-stored contexts with the FP64 inversion: overwrite
+// what moments_dev_kernel wrote with the FP64 inversion of the same delta.
+template <class O>
+void launch_closure_x64(lbm_ctx* c, const ProbDev& P, O* const o[6]) {
+  const unsigned g = blocks_for((int64_t)P.nx * P.ny, 256);
+  if (c->prec == LBM_F32_DEV)
+    closure_x64_kernel<float, O><<<g, 256, 0, c->stream>>>((const float*)c->buf[c->cur], P, c->plane, c->lim,
+                                                            c->limf, o[3], o[4], o[5]);
+  else
+    closure_x64_kernel<__nv_bfloat16, O><<<g, 256, 0, c->stream>>>((const __nv_bfloat16*)c->buf[c->cur], P,
+                                                                    c->plane, c->lim, c->limf, o[3], o[4], o[5]);
 }
 
 lbm_status ensure_tmp(lbm_ctx* ctx, int64_t doubles) {
@@ -354,6 +376,11 @@ lbm_status moments_impl(lbm_ctx* ctx, int32_t problem, O* const user[6], int32_t
   }
   CKL();
   ctx->launches += 1;
+  if (ctx->dim == 2 && ctx->prec != LBM_F64 && ctx->inv == LBM_INV_EXACT_F64 && (o[3] || o[4] || o[5])) {
+    launch_closure_x64<O>(ctx, P, o);
+    CKL();
+    ctx->launches += 1;
+  }
   if (diag) {
     reduce_partials_kernel<<<1, 256, 0, ctx->stream>>>(ctx->partials, g, ctx->diag_d);
     CKL();
@@ -413,7 +440,10 @@ lbm_status lbm_create(const lbm_params* p, void* cuda_stream, lbm_ctx** out) {
   if (p->order != 3) return fail(nullptr, LBM_EUNSUPPORTED, "lbm_create: only order K = 3 is implemented");
   if (p->stat < 0 || p->stat > 3) return fail(nullptr, LBM_EINVAL, "lbm_create: bad stat");
   if (p->prec < 0 || p->prec > 2) return fail(nullptr, LBM_EINVAL, "lbm_create: bad prec");
-  if (p->inv != LBM_INV_EXACT && p->inv != LBM_INV_SURROGATE) return fail(nullptr, LBM_EINVAL, "lbm_create: bad inv");
+  if (p->inv != LBM_INV_EXACT && p->inv != LBM_INV_SURROGATE && p->inv != LBM_INV_EXACT_F64)
+    return fail(nullptr, LBM_EINVAL, "lbm_create: bad inv");
+  if (p->inv == LBM_INV_EXACT_F64 && (p->stat != LBM_STAT_FD || p->dim != 2))
+    return fail(nullptr, LBM_EUNSUPPORTED, "lbm_create: the FP64 inversion applies to LBM_STAT_FD on d2v9");
   if (p->inv == LBM_INV_SURROGATE && (p->prec == LBM_F64 || p->stat != LBM_STAT_FD || p->dim != 2))
     return fail(nullptr, LBM_EUNSUPPORTED,
                 "lbm_create: the learned inversion needs LBM_STAT_FD with FP32 or BF16 deviation storage");

@@ -11,7 +11,9 @@ namespace lbm {
 
 // g = f_eq(n, u, t) - W_ref per cell, FP32 deviation form: the step's
 // relaxation with omega = 1 from g = 0 (g_eq = Delta W + W (S - 1), never f).
-template <class T, int STAT>
+// X64 (contexts with the FP64 inversion, FD statistics): the closure
+// delta = 3/2 - J_2(t) and J_4(t) in FP64, each rounded once to FP32.
+template <class T, int STAT, bool X64 = false>
 __global__ void init_dev_kernel(T* __restrict__ f, ProbDev P, int64_t plane, InitDesc d) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t cells = (int64_t)P.nx * P.ny;
@@ -27,7 +29,12 @@ __global__ void init_dev_kernel(T* __restrict__ f, ProbDev P, int64_t plane, Ini
     n = d.s[r][0]; ux = d.s[r][1]; uy = d.s[r][2]; t = d.s[r][3];
   }
   float delta, J4;
-  if (STAT == STAT_FD || STAT == STAT_FT) {
+  if (X64) {
+    double J2d, J4d;
+    closure_from_t<STAT_FD>(t, J2d, J4d);
+    delta = (float)(1.5 - J2d);
+    J4 = (float)J4d;
+  } else if (STAT == STAT_FD || STAT == STAT_FT) {
     closure_dev_from_t((float)t, delta, J4);
   } else {
     delta = (float)(1.5 - FixedJ<STAT>::j2);

@@ -21,7 +21,7 @@ from . import build as _build
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ETIMEOUT, LBM_EUNSUPPORTED = range(6)
 LBM_STAT_FD, LBM_STAT_FD_T0, LBM_STAT_MB, LBM_STAT_FT = range(4)
 LBM_F64, LBM_F32_DEV, LBM_BF16_DEV = range(3)
-LBM_INV_EXACT, LBM_INV_SURROGATE = range(2)
+LBM_INV_EXACT, LBM_INV_SURROGATE, LBM_INV_EXACT_F64 = range(3)
 LBM_BC_PERIODIC, LBM_BC_BOUNCEBACK = range(2)
 LBM_INIT_HALF, LBM_INIT_QUADRANT, LBM_INIT_FIELD = range(3)
 
@@ -163,7 +163,8 @@ def lbm_create(problems, stat="fd", prec="f64", inv="exact", stream=None, dim=2)
     dim 2: d2v9, dim 1: d1v3 (ny = 1)."""
     stat_c = _choice("closure", stat, STAT)
     prec_c = _choice("storage", prec, PREC)
-    inv_c = _choice("inversion", inv, {"exact": LBM_INV_EXACT, "surrogate": LBM_INV_SURROGATE})
+    inv_c = _choice("inversion", inv, {"exact": LBM_INV_EXACT, "surrogate": LBM_INV_SURROGATE,
+                                         "exact_f64": LBM_INV_EXACT_F64})
     for p in problems:
         for k in ("bc_x", "bc_y"):
             _choice("boundary", p.get(k, "periodic"), BC)

@@ -48,8 +48,9 @@ def test_oracle_worker_restarts_windows_and_counts_timed_steps():
     a = args("smooth_t")
     jobs, _ = bench.oracle_jobs(a, 1)
     job = dict(jobs[0], steps=30, warmup=1, window_steps=25)
-    updates, secs, steps = bench._oracle_window_worker(job)
+    updates, secs, steps, bad = bench._oracle_window_worker(job)
     assert steps == 30 and updates == 30 * job["f0"][0].size and secs > 0
+    assert bad == 0  # both windows end in a finite state
 
 
 @pytest.mark.parametrize("workload", ["smooth_t", "batched", "d1v3", "porous"])

@@ -165,3 +165,21 @@ def test_binding_rejects_unknown_names(lib, kw, msg):
         lib.lbm_create([dict(p, bc_x="wall")])
     with pytest.raises(ValueError, match="engine"):
         lib.lbm_surrogate_engine(None, "tcgen05")
+
+
+def test_create_rejects_fp64_inversion_misuse(lib):
+    """LBM_INV_EXACT_F64 exists for the FD closure on d2v9 only; an unknown
+    inversion is invalid.  Every check happens before any CUDA call."""
+    import ctypes as C
+
+    ctx = C.c_void_p()
+    arr = (lib.lbm_problem * 1)(lib.lbm_problem(64, 4, 0.8, 0, 0, 1.0, 0.05))
+    for stat in ("t0", "mb", "ft"):
+        par = lib.lbm_params(2, 3, lib.STAT[stat], 1, lib.LBM_INV_EXACT_F64, 1, arr)
+        assert lib.LIB.lbm_create(C.byref(par), None, C.byref(ctx)) == lib.LBM_EUNSUPPORTED
+        assert "FP64 inversion" in lib.lbm_last_error(None)
+    arr1 = (lib.lbm_problem * 1)(lib.lbm_problem(64, 1, 0.8, 0, 0, 1.0, 0.05))
+    par = lib.lbm_params(1, 3, lib.STAT["t0"], 1, lib.LBM_INV_EXACT_F64, 1, arr1)
+    assert lib.LIB.lbm_create(C.byref(par), None, C.byref(ctx)) == lib.LBM_EUNSUPPORTED
+    par = lib.lbm_params(2, 3, lib.STAT["fd"], 1, 3, 1, arr)
+    assert lib.LIB.lbm_create(C.byref(par), None, C.byref(ctx)) == lib.LBM_EINVAL
