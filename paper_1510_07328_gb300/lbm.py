@@ -415,15 +415,17 @@ class Lattice:
 
     def __init__(self, problems, stat="fd", prec="f64", stream=None, t_ref=None, n_ref=None, inv="exact",
                  surrogate=None, dim=2, engine=None, theta=None):
-        """theta: the fixed temperature of stat "ft" (sets t_ref = 2 pi theta/n_ref)."""
+        """theta: the fixed temperature of stat "ft" (sets t_ref = 2 pi theta/n_ref),
+        one value for every problem or a sequence with one per problem."""
         self.problems = list(problems)
         self.q = 9 if dim == 2 else 3
         descs = []
-        for p in self.problems:
+        for i, p in enumerate(self.problems):
             tr = t_ref if t_ref is not None else float(np.median(p.t)) if stat in ("fd", "ft") else 0.05
             nr = n_ref if n_ref is not None else float(np.mean(p.n))
             if theta is not None:
-                tr = 2.0 * np.pi * theta / nr
+                th = float(theta[i]) if np.ndim(theta) else float(theta)
+                tr = 2.0 * np.pi * th / nr
             descs.append(dict(nx=p.nx, ny=p.ny, tau=p.tau, bc_x=p.bc_x, bc_y=p.bc_y, n_ref=nr,
                               t_ref=min(max(tr, 1e-3), 10.0)))
         self.ctx = lbm_create(descs, stat, prec, inv=inv, stream=stream, dim=dim)
