@@ -82,13 +82,16 @@ def tol_for(prec, fmax, gmax):
     return K * (8 * u * gmax + 4e-6 * fmax)
 
 
-@pytest.mark.parametrize("prec", ["f32", "f64"])
-def test_smooth_t_4096_sampled(L, prec):
+@pytest.mark.parametrize("prec,inv", [("f32", "exact"), ("f64", "exact"), ("bf16", "exact"),
+                                      ("f32", "exact_f64")])
+def test_smooth_t_4096_sampled(L, prec, inv):
+    """The bench's lattice and contexts: FP32, FP64 and BF16 storage with the
+    exact inversion, and FP32 storage with the FP64 inversion."""
     import torch
 
     prob = inputs.smooth_t(4096, tau=0.8)
     dev = {k: torch.from_numpy(getattr(prob, k)).cuda() for k in ("n", "ux", "uy", "t")}
-    lat = L.Lattice([prob], stat="fd", prec=prec, n_ref=0.9, t_ref=0.05)  # as bench.py
+    lat = L.Lattice([prob], stat="fd", prec=prec, n_ref=0.9, t_ref=0.05, inv=inv)  # as bench.py
     lat.init(fields_on_device=dev)
     lat.step(K)
     cells = sample_cells(prob.nx, prob.ny, 48, seed=101)
