@@ -419,6 +419,8 @@ class Lattice:
         one value for every problem or a sequence with one per problem."""
         self.problems = list(problems)
         self.q = 9 if dim == 2 else 3
+        if theta is not None and np.ndim(theta) and len(theta) != len(self.problems):
+            raise ValueError(f"theta: {len(theta)} values for {len(self.problems)} problems")
         descs = []
         for i, p in enumerate(self.problems):
             tr = t_ref if t_ref is not None else float(np.median(p.t)) if stat in ("fd", "ft") else 0.05

@@ -183,3 +183,13 @@ def test_create_rejects_fp64_inversion_misuse(lib):
     assert lib.LIB.lbm_create(C.byref(par), None, C.byref(ctx)) == lib.LBM_EUNSUPPORTED
     par = lib.lbm_params(2, 3, lib.STAT["fd"], 1, 3, 1, arr)
     assert lib.LIB.lbm_create(C.byref(par), None, C.byref(ctx)) == lib.LBM_EINVAL
+
+
+def test_lattice_rejects_theta_count_mismatch(lib):
+    """A per-problem theta list must hold one value per problem; the check
+    runs in the binding, before any context exists."""
+    from paper_1510_07328_gb300 import inputs
+
+    probs = [inputs.riemann_1d(), inputs.riemann_1d(nx=64)]
+    with pytest.raises(ValueError, match="theta"):
+        lib.Lattice(probs, stat="ft", prec="f64", theta=[0.01])
