@@ -209,7 +209,7 @@ void launch_step(lbm_ctx* c, const void* in, void* out, cudaStream_t s) {
     return;
   }
   if (c->inv == LBM_INV_EXACT_F64 && c->prec != LBM_F64) {  // deviation storage, FP64 inversion
-    launch_step_x64(c->prec, c->rows, grid, s, a);
+    launch_step_x64(c->prec == LBM_F32_DEV, c->rows, grid, s, a);
     return;
   }
   switch (c->prec) {

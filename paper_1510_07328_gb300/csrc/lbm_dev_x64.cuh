@@ -91,7 +91,7 @@ __global__ void closure_x64_kernel(const T* __restrict__ f, ProbDev P, int64_t p
   if (ot) ot[i] = (O)t;
 }
 
-// Launcher of the step (prec: LBM_F32_DEV or LBM_BF16_DEV), step_x64.cu.
-void launch_step_x64(int prec, int rows, unsigned grid, cudaStream_t s, const StepArgs& a);
+// Launcher of the step for FP32 (f32) or BF16 deviations, step_x64.cu.
+void launch_step_x64(bool f32, int rows, unsigned grid, cudaStream_t s, const StepArgs& a);
 
 }  // namespace lbm

@@ -24,8 +24,8 @@ static void by_rows(int rows, unsigned grid, cudaStream_t s, const StepArgs& a) 
   }
 }
 
-void launch_step_x64(int prec, int rows, unsigned grid, cudaStream_t s, const StepArgs& a) {
-  if (prec == 1)
+void launch_step_x64(bool f32, int rows, unsigned grid, cudaStream_t s, const StepArgs& a) {
+  if (f32)
     by_rows<float>(rows, grid, s, a);
   else
     by_rows<__nv_bfloat16>(rows, grid, s, a);
