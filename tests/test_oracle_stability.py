@@ -158,3 +158,32 @@ def test_fixed_theta_riemann_1000_steps_stay_finite():
     assert 0.79 < n.min() and n.max() < 1.01
     jy = (f[2] - f[4] + f[5] + f[6] - f[7] - f[8]).sum()
     assert abs(jy) < 1e-11
+
+
+def test_fixed_theta_nonlinear_shock_diverges_at_low_tau():
+    """Linear stability in 1D does not hold for the nonlinear shock: the
+    batched workload's problem 181 (n = 1.82 | 1.0, t = 0.013, tau = 0.553),
+    on a 256 x 4 cut with walls at its x ends, under the fixed-theta closure
+    with theta = n_mean t/(2 pi), leaves the range of its two states by step
+    100 (the oracle measured the first non-finite or negative density at
+    step 86), while a milder problem of the same workload (116: ratio 2.0,
+    t = 0.107, tau = 0.656) stays within 2 % of that range."""
+    from paper_1510_07328_gb300 import inputs
+
+    specs = inputs.batched_specs()
+
+    def run(i, steps):
+        s = specs[i]
+        n = np.where(np.arange(256) < 128, s.n_left, s.n_right)[None, :].repeat(4, 0)
+        z = np.zeros_like(n)
+        th = 0.5 * (s.n_left + s.n_right) * s.t / (2 * math.pi)
+        f = lbm.init_equilibrium(n, z, z, 2 * math.pi * th / n, "ft")
+        p = lbm.Params(tau=s.tau, bc_x="bounceback", bc_y="periodic", stat="ft", theta=th)
+        with np.errstate(all="ignore"):
+            f = lbm.run(f, p, steps)
+        return f.sum(axis=0), min(s.n_left, s.n_right), max(s.n_left, s.n_right)
+
+    nn, lo, hi = run(181, 100)
+    assert not (np.isfinite(nn).all() and 0.98 * lo <= nn.min() and nn.max() <= 1.02 * hi)
+    nn, lo, hi = run(116, 100)
+    assert np.isfinite(nn).all() and 0.98 * lo <= nn.min() and nn.max() <= 1.02 * hi
