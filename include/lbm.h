@@ -349,11 +349,15 @@ lbm_status lbm_surrogate_load(lbm_ctx* ctx, const float* params);
  *  - LBM_SURROGATE_TENSOR_CORES (the default): its three layers as tcgen05
  *    MMAs over a tile row of 128 cells, FP16 operands with the inputs,
  *    layer-1 and layer-3 weights and all biases split into FP16 hi + lo
- *    parts, FP32 accumulation in tensor memory, SiLU in packed FP16;
+ *    parts, FP16 accumulation in tensor memory for the two hidden layers and
+ *    FP32 for the output layer, SiLU in packed FP16 (a quarter of the pairs
+ *    by a polynomial on the FMA pipe, the rest by the MUFU tanh);
  *  - LBM_SURROGATE_WARP_MMA: the same network, operands and splits, each warp
  *    on its own 32 cells with warp-level MMAs (mma.sync m16n8k8 / m16n8k16),
- *    FP32 accumulators in registers (layer-2 and layer-3 biases as FP32
- *    initial values), activations passed from layer to layer in registers;
+ *    FP16 accumulators in registers for the hidden layers (the layer-2 bias
+ *    as their initial value) and FP32 ones for the output layer (its bias as
+ *    the initial value), activations passed from layer to layer in
+ *    registers;
  *  - LBM_SURROGATE_FP32_PIPE: per cell on the FP32 pipe (FP32 throughout).
  * In every case the network's x = mu/T is polished by one third-order step on
  * J_2(x) = J_2 (one evaluation of f_0..f_4) and accepted when the first-order
